@@ -1,0 +1,118 @@
+"""Writer (and reader, for round-trip tests) of the neutral block file through
+which the GPU library imports an oracle H-matrix, its leaf order and, when
+given, its scaling coefficients.  Little-endian; complex numbers as (re, im)
+float64 pairs; every matrix row-major.
+
+  magic      8 bytes  b"HMPSBLK1"
+  int64      N, n_leaves, n_near, n_far, reading (0 = A, 1 = B, -1 = none), has_scaling
+  float64    wavelength, k
+  int64      perm[N]                     leaf position -> original RWG index
+  int64      leaf_off[n_leaves + 1]
+  near x n_near:   int64 i, j (i <= j);  complex128 block[m_i * m_j]
+  far  x n_far:    int64 kind (0 low rank, 1 dense), r0, m, c0, n, rank;
+                   kind 0: U[m * rank], V[n * rank]  (block = U V^T)
+                   kind 1: B[m * n]
+  if has_scaling:
+    int64 n_alpha
+    per leaf k: int64 count, int64 j[count]   (the stored row of alpha)
+    alpha blocks in that order: complex128 [m_k * m_j]
+    Dinv per leaf: complex128 [m_k * m_k]
+
+Parity unpinned beyond the round trip: this is a file format, not arithmetic.
+"""
+import struct
+
+import numpy as np
+
+MAGIC = b"HMPSBLK1"
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.complex128).tobytes()
+
+
+def write_blocks(path, H, S=None):
+    m = np.diff(H.leaf_off)
+    with open(path, "wb") as f:
+        f.write(MAGIC)
+        reading = -1 if S is None else (0 if S.reading == "A" else 1)
+        f.write(struct.pack("<6q", H.N, H.n_leaves, len(H.near), len(H.far),
+                            reading, 0 if S is None else 1))
+        f.write(struct.pack("<2d", float(H.meta.get("wavelength", 1.0)), float(H.k)))
+        f.write(np.ascontiguousarray(H.perm, dtype="<i8").tobytes())
+        f.write(np.ascontiguousarray(H.leaf_off, dtype="<i8").tobytes())
+        for (i, j) in sorted(H.near):
+            f.write(struct.pack("<2q", i, j))
+            f.write(_c(H.near[(i, j)]))
+        for kind, r0, mm, c0, n, P, Q in H.far:
+            if kind == "lr":
+                f.write(struct.pack("<6q", 0, r0, mm, c0, n, P.shape[1]))
+                f.write(_c(P))
+                f.write(_c(Q))
+            else:
+                f.write(struct.pack("<6q", 1, r0, mm, c0, n, 0))
+                f.write(_c(P))
+        if S is not None:
+            f.write(struct.pack("<q", len(S.alpha)))
+            for k in range(S.n):
+                f.write(struct.pack("<q", len(S.rows[k])))
+                f.write(np.asarray(S.rows[k], dtype="<i8").tobytes())
+            for k in range(S.n):
+                for j in S.rows[k]:
+                    f.write(_c(S.alpha[(k, j)]))
+            for k in range(S.n):
+                f.write(_c(S.Dinv[k]))
+
+
+def read_blocks(path):
+    """Inverse of write_blocks -> dict of numpy arrays (tests only)."""
+    buf = open(path, "rb").read()
+    assert buf[:8] == MAGIC
+    pos = 8
+
+    def take(fmt):
+        nonlocal pos
+        out = struct.unpack_from(fmt, buf, pos)
+        pos += struct.calcsize(fmt)
+        return out
+
+    def arr(dtype, count):
+        nonlocal pos
+        a = np.frombuffer(buf, dtype=dtype, count=count, offset=pos)
+        pos += a.nbytes
+        return a
+
+    N, nl, nn, nf, reading, has_s = take("<6q")
+    wl, k = take("<2d")
+    perm = arr("<i8", N)
+    off = arr("<i8", nl + 1)
+    m = np.diff(off)
+    near = {}
+    for _ in range(nn):
+        i, j = take("<2q")
+        near[(i, j)] = arr("<c16", m[i] * m[j]).reshape(m[i], m[j])
+    far = []
+    for _ in range(nf):
+        kind, r0, mm, c0, n, r = take("<6q")
+        if kind == 0:
+            far.append(("lr", r0, mm, c0, n, arr("<c16", mm * r).reshape(mm, r),
+                        arr("<c16", n * r).reshape(n, r)))
+        else:
+            far.append(("dense", r0, mm, c0, n, arr("<c16", mm * n).reshape(mm, n), None))
+    out = dict(N=N, perm=perm, leaf_off=off, near=near, far=far, k=k,
+               wavelength=wl, reading=reading)
+    if has_s:
+        (na,) = take("<q")
+        rows = []
+        for kk in range(nl):
+            (c,) = take("<q")
+            rows.append(arr("<i8", c).tolist())
+        alpha = {}
+        for kk in range(nl):
+            for j in rows[kk]:
+                alpha[(kk, j)] = arr("<c16", m[kk] * m[j]).reshape(m[kk], m[j])
+        dinv = [arr("<c16", m[kk] * m[kk]).reshape(m[kk], m[kk]) for kk in range(nl)]
+        assert len(alpha) == na
+        out.update(rows=rows, alpha=alpha, Dinv=dinv)
+    assert pos == len(buf)
+    return out

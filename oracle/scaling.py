@@ -1,0 +1,163 @@
+"""Schur-complement scaling of the symmetric near field (Sec. III-A,
+Eq. 14-29).
+
+For leaves k = 1..n in elimination order (the depth-first leaf order):
+  D_k      = Z~_kk                                   (the scaled diagonal block)
+  alpha_kj = -D_k^{-1} Z~_kj     for j > k in row k   (right coefficients, Eq. 16)
+  Z~_ij   += alpha_ki^T Z~_kj    for i <= j in row k  (Schur complement, Eq. 21:
+            = Z~_ij - Z~_ik D_k^{-1} Z~_kj, using Z~_ik = Z~_ki^T)
+The left coefficients are alpha' = alpha^T (Eq. 18 and the symmetry remark
+after Eq. 29) and are never stored.  After all n steps
+  R^T Z_N R = diag(D_1..D_n)  (Eq. 22-23),  R = alpha_1 alpha_2 ... alpha_n,
+R = (I - E)^{-1} with E_kj = alpha_kj (k < j), so x = R x~ is the block back
+substitution x_k = x~_k + sum_{j>k} alpha_kj x_j and b~ = R^T b is the forward
+substitution b~_j = b_j + sum_{k<j} alpha_kj^T b~_k (Eq. 25-26).
+
+Readings:
+  * "A" (default): the scaling considers every fill-in block (the block row of
+    k reaches all leaves that elimination connects to k), so Eq. 23 holds
+    exactly.  The pattern is the symbolic block Cholesky structure, computed
+    with the elimination tree (parent = first leaf in the row).
+  * "B": fill restricted to the near-field pattern; updates that land outside
+    it are dropped (the storage of the complexity analysis, Sec. IV).
+  * D_k^{-1} is LU with partial pivoting followed by the explicit inverse
+    (numpy.linalg.inv), FP64.
+
+Pinned by: the 4-block example of Eq. 14-21 (alpha_1 and the first Schur step
+block by block, blocks outside row/column 1 untouched), R^T Z_N R block
+diagonal with diagonal D (reading A), and the elimination-tree pattern equal
+to the naive all-pairs symbolic elimination.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Scaling:
+    n: int
+    rows: list           # rows[k] = sorted list of j > k with alpha_kj stored
+    alpha: dict          # (k, j) -> m_k x m_j
+    D: list              # D_k
+    Dinv: list           # D_k^{-1}
+    reading: str
+
+    def entries(self, leaf_off):
+        m = np.diff(leaf_off)
+        a = sum(int(m[k] * m[j]) for (k, j) in self.alpha)
+        d = int(np.sum(m * m))
+        return a, d
+
+
+def near_pattern(n, near_pairs):
+    rows = [set() for _ in range(n)]
+    for (i, j) in near_pairs:
+        if i < j:
+            rows[i].add(j)
+        elif j < i:
+            rows[j].add(i)
+    return rows
+
+
+def symbolic_fill(n, near_pairs):
+    """Block Cholesky structure: row(parent) |= row(k) - {parent}, parent =
+    min row(k), visiting k in order."""
+    rows = near_pattern(n, near_pairs)
+    for k in range(n):
+        if rows[k]:
+            p = min(rows[k])
+            rows[p] |= rows[k] - {p}
+    return [sorted(r) for r in rows]
+
+
+def symbolic_fill_naive(n, near_pairs):
+    """All-pairs elimination: eliminating k connects every pair of its row."""
+    rows = near_pattern(n, near_pairs)
+    for k in range(n):
+        lst = sorted(rows[k])
+        for a, i in enumerate(lst):
+            rows[i].update(lst[a + 1:])
+    return [sorted(r) for r in rows]
+
+
+def compute_scaling(H, reading="A"):
+    """Scaling coefficients of the H-matrix's near field (see module doc)."""
+    n = H.n_leaves
+    near_pairs = list(H.near.keys())
+    if reading == "A":
+        rows = symbolic_fill(n, near_pairs)
+    elif reading == "B":
+        rows = [sorted(r) for r in near_pattern(n, near_pairs)]
+    else:
+        raise ValueError(reading)
+    m = np.diff(H.leaf_off)
+    Zt = {}
+    for k in range(n):
+        Zt[(k, k)] = H.near[(k, k)].copy()
+        for j in rows[k]:
+            blk = H.near.get((k, j))
+            Zt[(k, j)] = blk.copy() if blk is not None else \
+                np.zeros((m[k], m[j]), np.complex128)
+    alpha, D, Dinv = {}, [], []
+    for k in range(n):
+        Dk = Zt.pop((k, k))
+        Dk_inv = np.linalg.inv(Dk)
+        D.append(Dk)
+        Dinv.append(Dk_inv)
+        row = rows[k]
+        for j in row:
+            alpha[(k, j)] = -Dk_inv @ Zt[(k, j)]
+        for a, i in enumerate(row):
+            aki_T = alpha[(k, i)].T
+            for j in row[a:]:
+                tgt = Zt.get((i, j))
+                if tgt is None:
+                    continue                      # reading B: outside the pattern
+                tgt += aki_T @ Zt[(k, j)]
+        for j in row:
+            del Zt[(k, j)]
+    return Scaling(n=n, rows=rows, alpha=alpha, D=D, Dinv=Dinv, reading=reading)
+
+
+# ------------------------------------------------------------ applications
+def apply_Rt(S, leaf_off, b):
+    """b~ = R^T b (Eq. 25) by forward block substitution, leaf order."""
+    out = np.array(b, dtype=np.complex128, copy=True)
+    sl = [slice(int(leaf_off[i]), int(leaf_off[i + 1])) for i in range(S.n)]
+    for k in range(S.n):
+        for j in S.rows[k]:
+            out[sl[j]] += S.alpha[(k, j)].T @ out[sl[k]]
+    return out
+
+
+def apply_R(S, leaf_off, x_t):
+    """x = R x~ (Eq. 26) by back block substitution, leaf order."""
+    out = np.array(x_t, dtype=np.complex128, copy=True)
+    sl = [slice(int(leaf_off[i]), int(leaf_off[i + 1])) for i in range(S.n)]
+    for k in range(S.n - 1, -1, -1):
+        for j in S.rows[k]:
+            out[sl[k]] += S.alpha[(k, j)] @ out[sl[j]]
+    return out
+
+
+def apply_Dinv(S, leaf_off, v):
+    """Z~_N^{-1} v, block by block (Eq. 32)."""
+    out = np.empty_like(v, dtype=np.complex128)
+    for k in range(S.n):
+        s = slice(int(leaf_off[k]), int(leaf_off[k + 1]))
+        out[s] = S.Dinv[k] @ v[s]
+    return out
+
+
+def dense_R(S, leaf_off):
+    """R = alpha_1 alpha_2 ... alpha_n as a dense matrix, multiplying the
+    dense alpha_k of Eq. 15-16 in order (small N only; tests)."""
+    N = int(leaf_off[-1])
+    R = np.eye(N, dtype=np.complex128)
+    for k in range(S.n):
+        Ak = np.eye(N, dtype=np.complex128)
+        sk = slice(int(leaf_off[k]), int(leaf_off[k + 1]))
+        for j in S.rows[k]:
+            Ak[sk, int(leaf_off[j]):int(leaf_off[j + 1])] = S.alpha[(k, j)]
+        R = R @ Ak
+    return R
