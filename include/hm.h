@@ -1,0 +1,156 @@
+/*
+ * hm.h -- C ABI of the GB300 power-series H-matrix EFIE solver.
+ *
+ * Method: Negi, Balakrishnan, Rao, "Fast Power Series Solution of Large 3-D
+ * Electrodynamic Integral Equation for PEC Scatterers" (arXiv 2109.04129).
+ * The system is the EFIE method-of-moments system [Z] x = b (Eq. 9) for a
+ * perfectly conducting surface, Galerkin tested with RWG functions (Sec. II),
+ * stored as an H-matrix Z = Z_N + Z_F (Eq. 13) and solved by the two-term
+ * power series of the near-field-scaled system (Eq. 24-36).
+ *
+ * Conventions for every entry point:
+ *  - No exception or C++ type crosses this boundary; every call returns an
+ *    hm_status.  Pointers named *_host are host memory; X and B of
+ *    hm_power_series_solve / hm_apply / hm_plane_wave_rhs are DEVICE memory
+ *    owned by the caller (the library never frees them).
+ *  - Complex vectors are complex128 interleaved (re, im), column-major
+ *    N x nrhs (column r starts at element r*N), in ORIGINAL RWG order
+ *    (unknown n = n-th interior edge in ascending (min vertex, max vertex)).
+ *  - Device work is ordered on the stream given to hm_set_stream (default:
+ *    the legacy default stream).  Calls that return values to the host
+ *    synchronise that stream.  A device-side error (a bounded wait that timed
+ *    out, a singular block) is reported by the next synchronising call.
+ *  - Required order: hm_build or hm_import -> hm_compute_scaling (unless the
+ *    imported file carries scaling) -> solves.  Otherwise HM_ERR_STATE.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns HM_ERR_CUDA.
+ */
+#ifndef HM_H
+#define HM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_ctx* hm_handle;   /* opaque; owns all device storage */
+
+typedef enum {
+  HM_OK = 0,
+  HM_ERR_INVALID = 1,    /* bad argument, malformed mesh or file          */
+  HM_ERR_CUDA = 2,       /* CUDA runtime error or no device               */
+  HM_ERR_OOM = 3,        /* device or host allocation failed             */
+  HM_ERR_SINGULAR = 4,   /* a scaled diagonal block has no usable pivot  */
+  HM_ERR_TIMEOUT = 5,    /* a bounded device wait ran out                */
+  HM_ERR_STATE = 6,      /* call out of order                            */
+  HM_ERR_IO = 7,         /* file could not be read or written           */
+  HM_WARN_SERIES_RATIO = 100 /* solve done; some ||it_1||/||it_0|| > 0.1 (Eq. 45) */
+} hm_status;
+
+enum { HM_FP64 = 0,        /* every product in complex FP64                   */
+       HM_MIXED = 1 };     /* scaling/far products in low precision with FP32
+                              accumulation, D^-1 in FP64, FP64 refinement     */
+enum { HM_ORDER_DFS = 0,   /* leaves in octree depth-first (Morton) order    */
+       HM_ORDER_ND = 1 };  /* geometric nested dissection of the leaf graph  */
+enum { HM_FILL_FULL = 0,   /* scaling keeps every fill-in block (Eq. 23 exact) */
+       HM_FILL_NEAR = 1 }; /* fill restricted to the near-field pattern      */
+
+typedef struct {
+  double wavelength;     /* metres; k = 2 pi / wavelength                     */
+  int leaf_max;          /* octree leaf cap in unknowns (Sec. II, V-A)         */
+  int ordering;          /* HM_ORDER_*: elimination order of the leaves        */
+  double aca_tol;        /* ACA / recompression tolerance eps of Eq. 12        */
+  int fill;              /* HM_FILL_*                                          */
+  int n_terms;           /* terms of Eq. 36 kept (paper: 2)                    */
+  int precision;         /* HM_FP64 or HM_MIXED                                */
+  int refine_steps;      /* refinement steps on the FP64 residual (mixed: 1)   */
+  long long spin_limit;  /* iteration cap of every device-side wait           */
+  int reserved[8];
+} hm_params;
+
+/* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,
+ * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26. */
+void hm_default_params(hm_params* p);
+
+/* Build the H-matrix of a closed or open triangulated PEC surface (Sec. II:
+ * RWG basis, octree clusters, non-touching admissibility (Eq. 10), dense
+ * near blocks, ACA + recompression far blocks (Eq. 11-12)).
+ * verts_host: nv x 3 float64 metres; tris_host: nt x 3 int32, 0-based,
+ * counter-clockwise seen from outside.  Both are copied.  Fails with
+ * HM_ERR_INVALID for an empty mesh, an out-of-range index or an edge shared
+ * by more than two triangles. */
+hm_status hm_build(const double* verts_host, int nv, const int* tris_host, int nt,
+                   const hm_params* p, hm_handle* out);
+
+/* Load an H-matrix (and, if present, its scaling coefficients) from the
+ * neutral block file: leaf order, near blocks, low-rank far blocks, alpha,
+ * D^-1 (format in the package documentation).  p supplies the solve
+ * options; its tree options are ignored. */
+hm_status hm_import(const char* path, const hm_params* p, hm_handle* out);
+
+/* Write the handle's H-matrix and scaling in the same file format
+ * (checkpoint of the expensive set-up). */
+hm_status hm_save(hm_handle h, const char* path);
+
+/* Schur-complement scaling of the symmetric near field (Sec. III-A,
+ * Eq. 14-23): for each leaf k in elimination order D_k = Z~_kk,
+ * alpha_kj = -D_k^-1 Z~_kj, Z~_ij += alpha_ki^T Z~_kj; stores alpha and
+ * D_k^-1 (FP64, LU with partial pivoting).  HM_ERR_SINGULAR if a pivot
+ * vanishes. */
+hm_status hm_compute_scaling(hm_handle h);
+
+/* Power-series solve of Z X = B (Eq. 25-36):
+ *   b~ = R^T b, b_o = D^-1 b~, w = D^-1 R^T Z_F R b_o, X = R (b_o - w)
+ * (n_terms = 2; more terms continue the alternating series).  In HM_MIXED
+ * the chain runs in low precision and refine_steps FP64 residual
+ * corrections follow.  X, B: device, N x nrhs complex128, original order;
+ * B is not modified; X is overwritten.  Returns HM_WARN_SERIES_RATIO (with X
+ * valid) when a ratio of Eq. 45 exceeds 0.1. */
+hm_status hm_power_series_solve(hm_handle h, void* X, const void* B, int nrhs);
+
+/* Same solve for HOST buffers: copies B in, solves, copies X out (pinned or
+ * pageable memory; synchronous). */
+hm_status hm_power_series_solve_host(hm_handle h, void* X_host, const void* B_host,
+                                     int nrhs);
+
+/* One step of the chain, for per-kernel checks.  Y = op(X), original order,
+ * device buffers, N x nrhs complex128:
+ *   HM_OP_RT   Y = R^T X      (Eq. 25)       HM_OP_R    Y = R X   (Eq. 26)
+ *   HM_OP_DINV Y = Z~_N^-1 X  (Eq. 32)       HM_OP_FAR  Y = Z_F X (Eq. 13)
+ *   HM_OP_NEAR Y = Z_N X                      HM_OP_Z    Y = (Z_N + Z_F) X
+ * op is applied in the handle's precision. */
+enum { HM_OP_RT = 0, HM_OP_R = 1, HM_OP_DINV = 2, HM_OP_FAR = 3, HM_OP_NEAR = 4,
+       HM_OP_Z = 5 };
+hm_status hm_apply(hm_handle h, int op, void* Y, const void* X, int nrhs);
+
+/* Plane-wave excitation b_m = <f_m, E_inc> (Eq. 2 tested), device output
+ * B (N x nrhs complex128).  theta_host/phi_host: incidence angles in radians
+ * (E_inc = p exp(-j k khat.r), khat = -(sin t cos p, sin t sin p, cos t));
+ * pol_host: 0 = theta-hat, 1 = phi-hat. */
+hm_status hm_plane_wave_rhs(hm_handle h, const double* theta_host, const double* phi_host,
+                            const int* pol_host, int nrhs, void* B);
+
+hm_status hm_set_stream(hm_handle h, void* cuda_stream);
+hm_status hm_num_unknowns(hm_handle h, int* n);
+
+/* Per-RHS diagnostics of the last solve (host arrays of length nrhs, either
+ * may be NULL): ratio_host[r] = ||it_1|| / ||it_0|| (Eq. 45); resid_host[r] =
+ * ||B - Z X|| / ||B|| after refinement (0 when no refinement ran). */
+hm_status hm_get_diagnostics(hm_handle h, double* ratio_host, double* resid_host, int nrhs);
+
+/* Counts, as long long, in this order (up to n of them): N, leaves, near
+ * blocks (upper), far blocks (upper), alpha entries, D entries, near entries
+ * (upper), far factor entries, max rank, forward levels, backward levels,
+ * device bytes held. */
+hm_status hm_get_stats(hm_handle h, long long* out_host, int n);
+
+/* Copy the leaf-order permutation (N int64, leaf position -> original index)
+ * and leaf offsets (leaves + 1 int64) to host arrays. */
+hm_status hm_get_tree(hm_handle h, long long* perm_host, long long* leaf_off_host);
+
+hm_status hm_destroy(hm_handle h);
+const char* hm_status_string(hm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HM_H */

@@ -1,0 +1,794 @@
+// C ABI of include/hm.h: handle life cycle, block-file import/export, the
+// level schedules of the sweeps, and the power-series solve chain.
+//
+// The solve follows Eq. 25-36 of the paper with R = alpha_1 ... alpha_n:
+//   b~ = R^T b  (forward block substitution, Eq. 25)
+//   b_o = Z~_N^{-1} b~ (Eq. 32), it_1 = Z~_N^{-1} R^T Z_F R b_o (Eq. 31)
+//   x = R (it_0 - it_1 + ...)  (Eq. 26, 36)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "hm_internal.h"
+#include "hm_mixed.h"
+
+using namespace hm;
+
+namespace hm {
+
+hm_status cuda_status(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return HM_ERR_OOM;
+  return HM_ERR_CUDA;
+}
+
+}  // namespace hm
+
+namespace {
+
+const long long KMAX = 512;   // inner rows per split-K task of a sweep
+
+template <class T>
+hm_status upload(T** dptr, const std::vector<T>& v, size_t* bytes) {
+  if (*dptr) cudaFree(*dptr);
+  *dptr = nullptr;
+  if (v.empty()) return HM_OK;
+  HM_CUDA(cudaMalloc((void**)dptr, v.size() * sizeof(T)));
+  HM_CUDA(cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (bytes) *bytes += v.size() * sizeof(T);
+  return HM_OK;
+}
+
+hm_status upload_tasks(TaskList& tl, size_t* bytes) {
+  hm_status s = upload(&tl.d_tasks, tl.tasks, bytes);
+  if (s != HM_OK) return s;
+  return upload(&tl.d_items, tl.items, bytes);
+}
+hm_status upload_fin(FinList& fl, size_t* bytes) {
+  hm_status s = upload(&fl.d_tasks, fl.tasks, bytes);
+  if (s != HM_OK) return s;
+  return upload(&fl.d_slots, fl.slots, bytes);
+}
+void free_tasks(TaskList& tl) {
+  cudaFree(tl.d_tasks);
+  cudaFree(tl.d_items);
+  tl.d_tasks = nullptr;
+  tl.d_items = nullptr;
+}
+void free_sweep(Sweep& sw) {
+  for (auto& t : sw.part) free_tasks(t);
+  for (auto& f : sw.fin) {
+    cudaFree(f.d_tasks);
+    cudaFree(f.d_slots);
+  }
+  sw.part.clear();
+  sw.fin.clear();
+}
+
+// One sweep over the alpha pattern.  forward: b~_j += sum_k alpha_kj^T b~_k
+// (targets j, predecessors k < j); backward: x_k += sum_j alpha_kj x_j
+// (targets k, successors j > k).  Levels: a target waits for all of its
+// sources.  Each target's sources are split into tasks of <= KMAX inner rows
+// writing scratch panels; the finalize adds them to the target in place.
+void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
+  const int n = h->nl;
+  std::vector<std::vector<std::pair<int, long long>>> src(n);   // (source leaf, alpha index)
+  for (int k = 0; k < n; ++k) {
+    long long base = h->alpha_row_start[k];
+    for (size_t q = 0; q < h->rows[k].size(); ++q) {
+      int j = h->rows[k][q];
+      if (forward)
+        src[j].push_back({k, base + (long long)q});
+      else
+        src[k].push_back({j, base + (long long)q});
+    }
+  }
+  std::vector<int> lev(n, 0);
+  int nlev = 0;
+  if (forward) {
+    for (int j = 0; j < n; ++j) {
+      for (auto& s : src[j]) lev[j] = std::max(lev[j], lev[s.first] + 1);
+      nlev = std::max(nlev, lev[j] + 1);
+    }
+  } else {
+    for (int k = n - 1; k >= 0; --k) {
+      for (auto& s : src[k]) lev[k] = std::max(lev[k], lev[s.first] + 1);
+      nlev = std::max(nlev, lev[k] + 1);
+    }
+  }
+  std::vector<std::vector<int>> bylev(nlev);
+  for (int t = 0; t < n; ++t) bylev[lev[t]].push_back(t);
+  sw.part.assign(nlev, TaskList());
+  sw.fin.assign(nlev, FinList());
+  int max_scr = 0;
+  for (int l = 0; l < nlev; ++l) {
+    TaskList& tl = sw.part[l];
+    FinList& fl = sw.fin[l];
+    int scr_row = 0;
+    for (int t : bylev[l]) {
+      if (src[t].empty()) continue;
+      const int mt = h->m[t];
+      FTask ft{VB_OUT, (int)h->leaf_off[t], mt, VB_OUT, (int)h->leaf_off[t],
+               (int)fl.slots.size(), 0};
+      size_t q = 0;
+      while (q < src[t].size()) {
+        GTask task{VB_SCR, scr_row, mt, (int)tl.items.size(), 0, 0, 0, 0};
+        long long kk = 0;
+        while (q < src[t].size() && (kk == 0 || kk + h->m[src[t][q].first] <= KMAX)) {
+          int s = src[t][q].first;
+          long long ai = src[t][q].second;
+          GItem it;
+          it.a_off = h->alpha_off[ai];
+          it.a_buf = AB_ALPHA;
+          if (forward) {   // alpha_st is m_s x m_t; need alpha^T: trans read
+            it.lda = mt;
+            it.trans = 1;
+          } else {         // alpha_ts is m_t x m_s
+            it.lda = h->m[s];
+            it.trans = 0;
+          }
+          it.k = h->m[s];
+          it.in_buf = VB_OUT;
+          it.in_row = (int)h->leaf_off[s];
+          tl.items.push_back(it);
+          tl.flops += (long long)mt * h->m[s];
+          tl.a_bytes += (long long)mt * h->m[s] * 16;
+          kk += h->m[s];
+          ++q;
+        }
+        task.it1 = (int)tl.items.size();
+        tl.tasks.push_back(task);
+        fl.slots.push_back(scr_row);
+        scr_row += mt;
+      }
+      ft.s1 = (int)fl.slots.size();
+      fl.tasks.push_back(ft);
+    }
+    max_scr = std::max(max_scr, scr_row);
+  }
+  sw.scratch_rows = max_scr;
+}
+
+hm_status build_schedules(hm_ctx* h) {
+  free_sweep(h->fwd);
+  free_sweep(h->bwd);
+  free_tasks(h->dinv_tl);
+  free_tasks(h->far1_tl);
+  free_tasks(h->far2_tl);
+  free_tasks(h->near_tl);
+  h->fwd = Sweep();
+  h->bwd = Sweep();
+  h->dinv_tl = TaskList();
+  h->far1_tl = TaskList();
+  h->far2_tl = TaskList();
+  h->near_tl = TaskList();
+  const int n = h->nl;
+  size_t* b = &h->dev_bytes;
+  if (h->has_scaling) {
+    build_sweep(h, true, h->fwd);
+    build_sweep(h, false, h->bwd);
+    for (int k = 0; k < n; ++k) {
+      GTask t{VB_OUT, (int)h->leaf_off[k], h->m[k], (int)h->dinv_tl.items.size(), 0, 0, 0, 0};
+      GItem it{h->dinv_off[k], AB_DINV, h->m[k], 0, h->m[k], VB_IN, (int)h->leaf_off[k]};
+      h->dinv_tl.items.push_back(it);
+      t.it1 = (int)h->dinv_tl.items.size();
+      h->dinv_tl.tasks.push_back(t);
+      h->dinv_tl.flops += (long long)h->m[k] * h->m[k];
+      h->dinv_tl.a_bytes += (long long)h->m[k] * h->m[k] * 16;
+    }
+    for (auto& tl : h->fwd.part) { hm_status s = upload_tasks(tl, b); if (s) return s; }
+    for (auto& fl : h->fwd.fin) { hm_status s = upload_fin(fl, b); if (s) return s; }
+    for (auto& tl : h->bwd.part) { hm_status s = upload_tasks(tl, b); if (s) return s; }
+    for (auto& fl : h->bwd.fin) { hm_status s = upload_fin(fl, b); if (s) return s; }
+    hm_status s = upload_tasks(h->dinv_tl, b);
+    if (s) return s;
+  }
+  // far field: stage 1 per low-rank block, stage 2 per leaf
+  std::vector<int> trow(h->far.size(), -1);
+  int nt = 0;
+  for (size_t bi = 0; bi < h->far.size(); ++bi) {
+    const FarDesc& f = h->far[bi];
+    if (f.kind != 0 || f.rank == 0) continue;
+    trow[bi] = nt;
+    GTask t1{VB_FAR, nt, f.rank, (int)h->far1_tl.items.size(), 0, 0, 0, 0};
+    h->far1_tl.items.push_back(GItem{f.offV, AB_FAR, f.rank, 1, f.n, VB_IN, f.c0});
+    t1.it1 = (int)h->far1_tl.items.size();
+    h->far1_tl.tasks.push_back(t1);
+    GTask t2{VB_FAR, nt + f.rank, f.rank, (int)h->far1_tl.items.size(), 0, 0, 0, 0};
+    h->far1_tl.items.push_back(GItem{f.offU, AB_FAR, f.rank, 1, f.m, VB_IN, f.r0});
+    t2.it1 = (int)h->far1_tl.items.size();
+    h->far1_tl.tasks.push_back(t2);
+    h->far1_tl.flops += (long long)f.rank * (f.m + f.n);
+    h->far1_tl.a_bytes += (long long)f.rank * (f.m + f.n) * 16;
+    nt += 2 * f.rank;
+  }
+  h->far_t_rows = nt;
+  std::vector<std::vector<GItem>> per_leaf(n);
+  auto leaf_of = [&](long long row) {
+    return (int)(std::upper_bound(h->leaf_off.begin(), h->leaf_off.end(), row) -
+                 h->leaf_off.begin()) - 1;
+  };
+  for (size_t bi = 0; bi < h->far.size(); ++bi) {
+    const FarDesc& f = h->far[bi];
+    for (int l = leaf_of(f.r0); l < n && h->leaf_off[l] < f.r0 + f.m; ++l) {
+      long long dr = h->leaf_off[l] - f.r0;
+      if (f.kind == 0) {
+        if (f.rank == 0) continue;
+        per_leaf[l].push_back(GItem{f.offU + dr * f.rank, AB_FAR, f.rank, 0, f.rank, VB_FAR,
+                                    trow[bi]});
+      } else {
+        per_leaf[l].push_back(GItem{f.offU + dr * f.n, AB_FAR, f.n, 0, f.n, VB_IN, f.c0});
+      }
+    }
+    for (int l = leaf_of(f.c0); l < n && h->leaf_off[l] < f.c0 + f.n; ++l) {
+      long long dc = h->leaf_off[l] - f.c0;
+      if (f.kind == 0) {
+        if (f.rank == 0) continue;
+        per_leaf[l].push_back(GItem{f.offV + dc * f.rank, AB_FAR, f.rank, 0, f.rank, VB_FAR,
+                                    trow[bi] + f.rank});
+      } else {
+        per_leaf[l].push_back(GItem{f.offU + dc, AB_FAR, f.n, 1, f.m, VB_IN, f.r0});
+      }
+    }
+  }
+  for (int l = 0; l < n; ++l) {
+    GTask t{VB_OUT, (int)h->leaf_off[l], h->m[l], (int)h->far2_tl.items.size(), 0, 0, 0, 0};
+    for (auto& it : per_leaf[l]) {
+      h->far2_tl.items.push_back(it);
+      h->far2_tl.flops += (long long)h->m[l] * it.k;
+      h->far2_tl.a_bytes += (long long)h->m[l] * it.k * 16;
+    }
+    t.it1 = (int)h->far2_tl.items.size();
+    h->far2_tl.tasks.push_back(t);
+  }
+  // near field Z_N (upper blocks + transposes)
+  std::vector<std::vector<GItem>> near_leaf(n);
+  for (const NearDesc& d : h->near) {
+    near_leaf[d.i].push_back(GItem{d.off, AB_NEAR, h->m[d.j], 0, h->m[d.j], VB_IN,
+                                   (int)h->leaf_off[d.j]});
+    if (d.i != d.j)
+      near_leaf[d.j].push_back(GItem{d.off, AB_NEAR, h->m[d.j], 1, h->m[d.i], VB_IN,
+                                     (int)h->leaf_off[d.i]});
+  }
+  for (int l = 0; l < n; ++l) {
+    GTask t{VB_OUT, (int)h->leaf_off[l], h->m[l], (int)h->near_tl.items.size(), 0, 0, 0, 0};
+    for (auto& it : near_leaf[l]) {
+      h->near_tl.items.push_back(it);
+      h->near_tl.flops += (long long)h->m[l] * it.k;
+    }
+    t.it1 = (int)h->near_tl.items.size();
+    h->near_tl.tasks.push_back(t);
+  }
+  hm_status s = upload_tasks(h->far1_tl, b);
+  if (!s) s = upload_tasks(h->far2_tl, b);
+  if (!s) s = upload_tasks(h->near_tl, b);
+  if (s) return s;
+  h->sched_ready = true;
+  return HM_OK;
+}
+
+hm_status ensure_buffers(hm_ctx* h, int nrhs) {
+  if (nrhs <= h->cap_nrhs) return HM_OK;
+  for (int i = 0; i < NPHYS; ++i) {
+    cudaFree(h->d_vec[i]);
+    h->d_vec[i] = nullptr;
+  }
+  cudaFree(h->d_norms);
+  h->d_norms = nullptr;
+  h->cap_nrhs = 0;
+  size_t rows[NPHYS];
+  for (int i = 0; i < NPHYS; ++i) rows[i] = (size_t)h->N;
+  rows[P_SCR] = std::max<size_t>(1, std::max(h->fwd.scratch_rows, h->bwd.scratch_rows));
+  rows[P_FAR] = std::max<size_t>(1, h->far_t_rows);
+  for (int i = 0; i < NPHYS; ++i) {
+    HM_CUDA(cudaMalloc((void**)&h->d_vec[i], rows[i] * nrhs * sizeof(cplx)));
+    h->vec_rows[i] = rows[i];
+  }
+  HM_CUDA(cudaMalloc((void**)&h->d_norms, 4 * sizeof(double) * nrhs));
+  h->cap_nrhs = nrhs;
+  return HM_OK;
+}
+
+ABufs abufs(hm_ctx* h) {
+  ABufs a{};
+  a.p[AB_NEAR] = h->d_near;
+  a.p[AB_FAR] = h->d_far;
+  a.p[AB_ALPHA] = h->d_alpha;
+  a.p[AB_DINV] = h->d_dinv;
+  return a;
+}
+
+VBufs vbufs(hm_ctx* h, cplx* in, cplx* out) {
+  VBufs v{};
+  v.p[VB_IN] = in;
+  v.p[VB_OUT] = out;
+  v.p[VB_SCR] = h->d_vec[P_SCR];
+  v.p[VB_FAR] = h->d_vec[P_FAR];
+  return v;
+}
+
+hm_status run_sweep(hm_ctx* h, Sweep& sw, cplx* buf, int nrhs) {
+  VBufs v = vbufs(h, buf, buf);
+  for (size_t l = 0; l < sw.part.size(); ++l) {
+    hm_status s = launch_tasks(sw.part[l], v, abufs(h), nrhs, h->stream);
+    if (s) return s;
+    s = launch_fin(sw.fin[l], v, nrhs, h->stream);
+    if (s) return s;
+  }
+  return HM_OK;
+}
+
+hm_status run_list(hm_ctx* h, TaskList& tl, cplx* in, cplx* out, int nrhs) {
+  return launch_tasks(tl, vbufs(h, in, out), abufs(h), nrhs, h->stream);
+}
+
+hm_status copy_panel(hm_ctx* h, cplx* dst, const cplx* src, int nrhs) {
+  HM_CUDA(cudaMemcpyAsync(dst, src, (size_t)h->N * nrhs * sizeof(cplx),
+                          cudaMemcpyDeviceToDevice, h->stream));
+  return HM_OK;
+}
+
+hm_status apply_far(hm_ctx* h, cplx* in, cplx* out, int nrhs) {
+  hm_status s = run_list(h, h->far1_tl, in, out, nrhs);
+  if (s) return s;
+  return run_list(h, h->far2_tl, in, out, nrhs);
+}
+
+// x (leaf order, in-place in P_XT) from b (leaf order, P_B): FP64 chain.
+hm_status series_fp64(hm_ctx* h, int nrhs, bool diag) {
+  cplx** V = h->d_vec;
+  hm_status s;
+  // b~ = R^T b ; b_o = D^-1 b~
+  if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
+  if ((s = run_sweep(h, h->fwd, V[P_Y], nrhs))) return s;
+  if ((s = run_list(h, h->dinv_tl, V[P_Y], V[P_BO], nrhs))) return s;
+  if ((s = copy_panel(h, V[P_XT], V[P_BO], nrhs))) return s;
+  cplx* it = V[P_BO];
+  for (int t = 1; t < h->p.n_terms; ++t) {
+    // it_t = D^-1 R^T Z_F R it_{t-1}
+    if ((s = copy_panel(h, V[P_Y], it, nrhs))) return s;
+    if ((s = run_sweep(h, h->bwd, V[P_Y], nrhs))) return s;
+    if ((s = apply_far(h, V[P_Y], V[P_Z], nrhs))) return s;
+    if ((s = run_sweep(h, h->fwd, V[P_Z], nrhs))) return s;
+    cplx* nxt = (it == V[P_IT]) ? V[P_R] : V[P_IT];
+    if ((s = run_list(h, h->dinv_tl, V[P_Z], nxt, nrhs))) return s;
+    if (t == 1 && diag) {
+      if ((s = launch_col_norms2(it, h->N, nrhs, h->d_norms, h->stream))) return s;
+      if ((s = launch_col_norms2(nxt, h->N, nrhs, h->d_norms + nrhs, h->stream))) return s;
+    }
+    double sg = (t % 2) ? -1.0 : 1.0;
+    if ((s = launch_axpby(V[P_XT], V[P_XT], 1.0, nxt, sg, (size_t)h->N * nrhs, h->stream)))
+      return s;
+    it = nxt;
+  }
+  // x = R x~
+  return run_sweep(h, h->bwd, V[P_XT], nrhs);
+}
+
+hm_status check_ready(hm_ctx* h) {
+  if (!h) return HM_ERR_INVALID;
+  if (!h->has_scaling || !h->sched_ready) return HM_ERR_STATE;
+  return HM_OK;
+}
+
+// ---------------------------------------------------------------- file IO
+struct Reader {
+  FILE* f;
+  bool ok = true;
+  template <class T>
+  void get(T* p, size_t n) {
+    if (ok && fread(p, sizeof(T), n, f) != n) ok = false;
+  }
+  long long q() {
+    long long v = 0;
+    get(&v, 1);
+    return v;
+  }
+};
+
+hm_status finish_structure(hm_ctx* h) {
+  h->nl = (int)h->leaf_off.size() - 1;
+  h->m.resize(h->nl);
+  for (int i = 0; i < h->nl; ++i) h->m[i] = (int)(h->leaf_off[i + 1] - h->leaf_off[i]);
+  std::vector<int> perm32(h->perm.begin(), h->perm.end());
+  return upload(&h->d_perm, perm32, &h->dev_bytes);
+}
+
+}  // namespace
+
+namespace hm {
+hm_status upload_values(hm_ctx* h) {
+  size_t* b = &h->dev_bytes;
+  hm_status s = upload(&h->d_near, h->h_near, b);
+  if (!s) s = upload(&h->d_far, h->h_far, b);
+  if (!s) s = upload(&h->d_alpha, h->h_alpha, b);
+  if (!s) s = upload(&h->d_dinv, h->h_dinv, b);
+  return s;
+}
+hm_status rebuild_schedules(hm_ctx* h) { return build_schedules(h); }
+}  // namespace hm
+
+extern "C" {
+
+void hm_default_params(hm_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->wavelength = 1.0;
+  p->leaf_max = 64;
+  p->ordering = HM_ORDER_DFS;
+  p->aca_tol = 1e-4;
+  p->fill = HM_FILL_FULL;
+  p->n_terms = 2;
+  p->precision = HM_FP64;
+  p->refine_steps = 0;
+  p->spin_limit = 1LL << 26;
+}
+
+const char* hm_status_string(hm_status s) {
+  switch (s) {
+    case HM_OK: return "ok";
+    case HM_ERR_INVALID: return "invalid argument";
+    case HM_ERR_CUDA: return "CUDA error";
+    case HM_ERR_OOM: return "out of memory";
+    case HM_ERR_SINGULAR: return "singular diagonal block";
+    case HM_ERR_TIMEOUT: return "device wait timed out";
+    case HM_ERR_STATE: return "call out of order";
+    case HM_ERR_IO: return "file error";
+    case HM_WARN_SERIES_RATIO: return "series ratio above 0.1 (Eq. 45)";
+  }
+  return "unknown status";
+}
+
+hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
+  if (!path || !out) return HM_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return HM_ERR_CUDA;
+  FILE* f = fopen(path, "rb");
+  if (!f) return HM_ERR_IO;
+  hm_ctx* h = nullptr;
+  try {
+    h = new hm_ctx();
+    if (p) h->p = *p; else hm_default_params(&h->p);
+    cudaGetDevice(&h->dev);
+    Reader r{f};
+    char magic[8];
+    r.get(magic, 8);
+    if (!r.ok || memcmp(magic, "HMPSBLK1", 8) != 0) throw std::runtime_error("magic");
+    long long N = r.q(), nl = r.q(), nn = r.q(), nf = r.q(), reading = r.q(), has_s = r.q();
+    double wl = 0, kk = 0;
+    r.get(&wl, 1);
+    r.get(&kk, 1);
+    if (!r.ok || N <= 0 || nl <= 0 || N > (1LL << 30) || nl > N) throw std::runtime_error("hdr");
+    h->N = (int)N;
+    h->wavelength = wl;
+    h->k = kk;
+    h->perm.resize(N);
+    r.get(h->perm.data(), N);
+    h->leaf_off.resize(nl + 1);
+    r.get(h->leaf_off.data(), nl + 1);
+    if (!r.ok || h->leaf_off[0] != 0 || h->leaf_off[nl] != N) throw std::runtime_error("off");
+    for (long long i = 0; i < nl; ++i)
+      if (h->leaf_off[i + 1] <= h->leaf_off[i]) throw std::runtime_error("off");
+    std::vector<char> seen(N, 0);
+    for (long long i = 0; i < N; ++i) {
+      if (h->perm[i] < 0 || h->perm[i] >= N || seen[h->perm[i]]) throw std::runtime_error("perm");
+      seen[h->perm[i]] = 1;
+    }
+    hm_status s = finish_structure(h);
+    if (s) throw s;
+    for (long long b = 0; b < nn; ++b) {
+      long long i = r.q(), j = r.q();
+      if (!r.ok || i < 0 || j < i || j >= nl) throw std::runtime_error("near");
+      NearDesc d{(int)i, (int)j, (long long)h->h_near.size()};
+      size_t cnt = (size_t)h->m[i] * h->m[j];
+      h->h_near.resize(h->h_near.size() + cnt);
+      r.get(h->h_near.data() + d.off, cnt);
+      h->near.push_back(d);
+    }
+    for (long long b = 0; b < nf; ++b) {
+      long long kind = r.q(), r0 = r.q(), m = r.q(), c0 = r.q(), n = r.q(), rank = r.q();
+      if (!r.ok || kind < 0 || kind > 1 || r0 < 0 || c0 < 0 || m <= 0 || n <= 0 ||
+          r0 + m > N || c0 + n > N || rank < 0 || rank > std::min(m, n))
+        throw std::runtime_error("far");
+      FarDesc d{(int)kind, (int)r0, (int)m, (int)c0, (int)n, (int)rank, 0, 0};
+      d.offU = (long long)h->h_far.size();
+      if (kind == 0) {
+        d.offV = d.offU + m * rank;
+        h->h_far.resize(h->h_far.size() + (m + n) * rank);
+        r.get(h->h_far.data() + d.offU, (size_t)((m + n) * rank));
+      } else {
+        d.rank = 0;
+        h->h_far.resize(h->h_far.size() + m * n);
+        r.get(h->h_far.data() + d.offU, (size_t)(m * n));
+      }
+      h->far.push_back(d);
+    }
+    if (has_s) {
+      long long na = r.q();
+      h->rows.assign(nl, {});
+      h->alpha_row_start.assign(nl + 1, 0);
+      long long cnt_all = 0;
+      for (long long k = 0; k < nl; ++k) {
+        long long c = r.q();
+        if (!r.ok || c < 0 || c > nl) throw std::runtime_error("rows");
+        std::vector<long long> js(c);
+        r.get(js.data(), c);
+        for (long long q = 0; q < c; ++q) {
+          if (js[q] <= k || js[q] >= nl || (q && js[q] <= js[q - 1]))
+            throw std::runtime_error("rows");
+          h->rows[k].push_back((int)js[q]);
+        }
+        h->alpha_row_start[k] = cnt_all;
+        cnt_all += c;
+      }
+      h->alpha_row_start[nl] = cnt_all;
+      if (cnt_all != na) throw std::runtime_error("alpha count");
+      for (long long k = 0; k < nl; ++k)
+        for (int j : h->rows[k]) {
+          h->alpha_off.push_back((long long)h->h_alpha.size());
+          size_t cnt = (size_t)h->m[k] * h->m[j];
+          h->h_alpha.resize(h->h_alpha.size() + cnt);
+          r.get(h->h_alpha.data() + h->alpha_off.back(), cnt);
+        }
+      for (long long k = 0; k < nl; ++k) {
+        h->dinv_off.push_back((long long)h->h_dinv.size());
+        size_t cnt = (size_t)h->m[k] * h->m[k];
+        h->h_dinv.resize(h->h_dinv.size() + cnt);
+        r.get(h->h_dinv.data() + h->dinv_off.back(), cnt);
+      }
+      h->has_scaling = true;
+      h->p.fill = (reading == 1) ? HM_FILL_NEAR : HM_FILL_FULL;
+    }
+    char extra;
+    if (!r.ok || fread(&extra, 1, 1, f) != 0) throw std::runtime_error("size");
+    fclose(f);
+    f = nullptr;
+    s = upload_values(h);
+    if (s) throw s;
+    s = build_schedules(h);
+    if (s) throw s;
+    s = hm_mixed_prepare(h);
+    if (s) throw s;
+    *out = h;
+    return HM_OK;
+  } catch (hm_status s) {
+    if (f) fclose(f);
+    hm_destroy(h);
+    return s;
+  } catch (std::bad_alloc&) {
+    if (f) fclose(f);
+    hm_destroy(h);
+    return HM_ERR_OOM;
+  } catch (...) {
+    if (f) fclose(f);
+    hm_destroy(h);
+    return HM_ERR_IO;
+  }
+}
+
+hm_status hm_save(hm_handle h, const char* path) {
+  if (!h || !path) return HM_ERR_INVALID;
+  FILE* f = fopen(path, "wb");
+  if (!f) return HM_ERR_IO;
+  auto put = [&](const void* p, size_t sz) { return fwrite(p, 1, sz, f) == sz; };
+  bool ok = put("HMPSBLK1", 8);
+  long long reading = h->has_scaling ? (h->p.fill == HM_FILL_NEAR ? 1 : 0) : -1;
+  long long hdr[6] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), reading,
+                      h->has_scaling ? 1 : 0};
+  ok = ok && put(hdr, sizeof(hdr));
+  double d2[2] = {h->wavelength, h->k};
+  ok = ok && put(d2, sizeof(d2));
+  ok = ok && put(h->perm.data(), h->perm.size() * 8);
+  ok = ok && put(h->leaf_off.data(), h->leaf_off.size() * 8);
+  for (auto& d : h->near) {
+    long long ij[2] = {d.i, d.j};
+    ok = ok && put(ij, 16) &&
+         put(h->h_near.data() + d.off, (size_t)h->m[d.i] * h->m[d.j] * sizeof(cplx));
+  }
+  for (auto& d : h->far) {
+    long long hd[6] = {d.kind, d.r0, d.m, d.c0, d.n, d.rank};
+    ok = ok && put(hd, sizeof(hd));
+    size_t cnt = d.kind == 0 ? (size_t)(d.m + d.n) * d.rank : (size_t)d.m * d.n;
+    ok = ok && put(h->h_far.data() + d.offU, cnt * sizeof(cplx));
+  }
+  if (h->has_scaling) {
+    long long na = (long long)h->alpha_off.size();
+    ok = ok && put(&na, 8);
+    for (int k = 0; k < h->nl; ++k) {
+      long long c = (long long)h->rows[k].size();
+      ok = ok && put(&c, 8);
+      for (int j : h->rows[k]) {
+        long long jj = j;
+        ok = ok && put(&jj, 8);
+      }
+    }
+    size_t q = 0;
+    for (int k = 0; k < h->nl; ++k)
+      for (int j : h->rows[k])
+        ok = ok && put(h->h_alpha.data() + h->alpha_off[q++],
+                       (size_t)h->m[k] * h->m[j] * sizeof(cplx));
+    for (int k = 0; k < h->nl; ++k)
+      ok = ok && put(h->h_dinv.data() + h->dinv_off[k], (size_t)h->m[k] * h->m[k] * sizeof(cplx));
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? HM_OK : HM_ERR_IO;
+}
+
+hm_status hm_set_stream(hm_handle h, void* stream) {
+  if (!h) return HM_ERR_INVALID;
+  h->stream = (cudaStream_t)stream;
+  return HM_OK;
+}
+
+hm_status hm_num_unknowns(hm_handle h, int* n) {
+  if (!h || !n) return HM_ERR_INVALID;
+  *n = h->N;
+  return HM_OK;
+}
+
+hm_status hm_get_tree(hm_handle h, long long* perm, long long* off) {
+  if (!h) return HM_ERR_INVALID;
+  if (perm) memcpy(perm, h->perm.data(), h->perm.size() * 8);
+  if (off) memcpy(off, h->leaf_off.data(), h->leaf_off.size() * 8);
+  return HM_OK;
+}
+
+hm_status hm_apply(hm_handle h, int op, void* Y, const void* X, int nrhs) {
+  if (!h || !Y || !X || nrhs <= 0) return HM_ERR_INVALID;
+  if (op < HM_OP_RT || op > HM_OP_Z) return HM_ERR_INVALID;
+  if ((op == HM_OP_RT || op == HM_OP_R || op == HM_OP_DINV) && !h->has_scaling)
+    return HM_ERR_STATE;
+  try {
+    hm_status s = ensure_buffers(h, nrhs);
+    if (s) return s;
+    if (h->p.precision == HM_MIXED) return hm_mixed_apply(h, op, (cplx*)Y, (const cplx*)X, nrhs);
+    cplx** V = h->d_vec;
+    if ((s = launch_gather_perm((const cplx*)X, V[P_B], h->d_perm, h->N, nrhs, h->stream)))
+      return s;
+    cplx* res = V[P_Y];
+    switch (op) {
+      case HM_OP_RT:
+        if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
+        s = run_sweep(h, h->fwd, V[P_Y], nrhs);
+        break;
+      case HM_OP_R:
+        if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
+        s = run_sweep(h, h->bwd, V[P_Y], nrhs);
+        break;
+      case HM_OP_DINV: s = run_list(h, h->dinv_tl, V[P_B], V[P_Y], nrhs); break;
+      case HM_OP_FAR: s = apply_far(h, V[P_B], V[P_Y], nrhs); break;
+      case HM_OP_NEAR: s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs); break;
+      case HM_OP_Z:
+        s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs);
+        if (!s) s = apply_far(h, V[P_B], V[P_Z], nrhs);
+        if (!s)
+          s = launch_axpby(V[P_Y], V[P_Y], 1.0, V[P_Z], 1.0, (size_t)h->N * nrhs, h->stream);
+        break;
+    }
+    if (s) return s;
+    s = launch_scatter_perm(res, (cplx*)Y, h->d_perm, h->N, nrhs, h->stream);
+    if (s) return s;
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    return HM_OK;
+  } catch (std::bad_alloc&) {
+    return HM_ERR_OOM;
+  } catch (...) {
+    return HM_ERR_INVALID;
+  }
+}
+
+hm_status hm_power_series_solve(hm_handle h, void* X, const void* B, int nrhs) {
+  hm_status s = check_ready(h);
+  if (s) return s;
+  if (!X || !B || nrhs <= 0) return HM_ERR_INVALID;
+  if (h->p.n_terms < 1) return HM_ERR_INVALID;
+  try {
+    if ((s = ensure_buffers(h, nrhs))) return s;
+    if (h->p.precision == HM_MIXED) {
+      s = hm_mixed_solve(h, (cplx*)X, (const cplx*)B, nrhs);
+    } else {
+      cplx** V = h->d_vec;
+      if ((s = launch_gather_perm((const cplx*)B, V[P_B], h->d_perm, h->N, nrhs, h->stream)))
+        return s;
+      if ((s = series_fp64(h, nrhs, true))) return s;
+      s = launch_scatter_perm(V[P_XT], (cplx*)X, h->d_perm, h->N, nrhs, h->stream);
+      h->ratio.assign(nrhs, 0.0);
+      h->resid.assign(nrhs, 0.0);
+    }
+    if (s) return s;
+    h->last_nrhs = nrhs;
+    return HM_OK;
+  } catch (std::bad_alloc&) {
+    return HM_ERR_OOM;
+  } catch (...) {
+    return HM_ERR_INVALID;
+  }
+}
+
+hm_status hm_power_series_solve_host(hm_handle h, void* X_host, const void* B_host, int nrhs) {
+  hm_status s = check_ready(h);
+  if (s) return s;
+  if (!X_host || !B_host || nrhs <= 0) return HM_ERR_INVALID;
+  try {
+    if ((s = ensure_buffers(h, nrhs))) return s;
+    size_t bytes = (size_t)h->N * nrhs * sizeof(cplx);
+    cplx* dB = h->d_vec[P_HB];
+    cplx* dX = h->d_vec[P_HX];
+    HM_CUDA(cudaMemcpyAsync(dB, B_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    s = hm_power_series_solve(h, dX, dB, nrhs);
+    if (s != HM_OK && s != HM_WARN_SERIES_RATIO) return s;
+    HM_CUDA(cudaMemcpyAsync(X_host, dX, bytes, cudaMemcpyDeviceToHost, h->stream));
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    return s;
+  } catch (...) {
+    return HM_ERR_INVALID;
+  }
+}
+
+hm_status hm_get_diagnostics(hm_handle h, double* ratio, double* resid, int nrhs) {
+  if (!h || nrhs <= 0) return HM_ERR_INVALID;
+  if (nrhs > h->last_nrhs || !h->d_norms) return HM_ERR_STATE;
+  std::vector<double> nrm(4 * (size_t)h->cap_nrhs, 0.0);
+  HM_CUDA(cudaStreamSynchronize(h->stream));
+  HM_CUDA(cudaMemcpy(nrm.data(), h->d_norms, nrm.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  bool warn = false;
+  for (int r = 0; r < nrhs; ++r) {
+    double a = std::sqrt(nrm[r]), b = std::sqrt(nrm[h->last_nrhs + r]);
+    double q = (a > 0) ? b / a : 0.0;
+    if (ratio) ratio[r] = h->p.n_terms >= 2 ? q : 0.0;
+    if (q > 0.1 && h->p.n_terms >= 2) warn = true;
+    if (resid) {
+      double bb = nrm[2 * h->last_nrhs + r], rr = nrm[3 * h->last_nrhs + r];
+      resid[r] = (h->p.precision == HM_MIXED && h->p.refine_steps > 0 && bb > 0)
+                     ? std::sqrt(rr / bb) : 0.0;
+    }
+  }
+  return warn ? HM_WARN_SERIES_RATIO : HM_OK;
+}
+
+hm_status hm_get_stats(hm_handle h, long long* out, int n) {
+  if (!h || !out) return HM_ERR_INVALID;
+  long long near_e = 0, far_e = 0, maxr = 0, a_e = 0, d_e = 0;
+  for (auto& d : h->near) near_e += (long long)h->m[d.i] * h->m[d.j];
+  for (auto& d : h->far) {
+    far_e += d.kind == 0 ? (long long)(d.m + d.n) * d.rank : (long long)d.m * d.n;
+    maxr = std::max<long long>(maxr, d.rank);
+  }
+  for (int k = 0; k < (int)h->rows.size(); ++k)
+    for (int j : h->rows[k]) a_e += (long long)h->m[k] * h->m[j];
+  for (int k = 0; k < h->nl; ++k) d_e += (long long)h->m[k] * h->m[k];
+  long long v[12] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
+                     near_e, far_e, maxr, (long long)h->fwd.part.size(),
+                     (long long)h->bwd.part.size(), (long long)h->dev_bytes};
+  for (int i = 0; i < n && i < 12; ++i) out[i] = v[i];
+  return HM_OK;
+}
+
+hm_status hm_destroy(hm_handle h) {
+  if (!h) return HM_OK;
+  free_sweep(h->fwd);
+  free_sweep(h->bwd);
+  free_tasks(h->dinv_tl);
+  free_tasks(h->far1_tl);
+  free_tasks(h->far2_tl);
+  free_tasks(h->near_tl);
+  hm_mixed_release(h);
+  cudaFree(h->d_perm);
+  cudaFree(h->d_near);
+  cudaFree(h->d_far);
+  cudaFree(h->d_alpha);
+  cudaFree(h->d_dinv);
+  for (int i = 0; i < NPHYS; ++i) cudaFree(h->d_vec[i]);
+  cudaFree(h->d_norms);
+  cudaFree(h->d_verts);
+  cudaFree(h->d_tris);
+  cudaFree(h->d_edge);
+  delete h;
+  return HM_OK;
+}
+
+}  // extern "C"

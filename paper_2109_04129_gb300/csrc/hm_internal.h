@@ -1,0 +1,148 @@
+// Internal declarations of the GB300 power-series H-matrix solver library.
+// Everything here stays behind the C ABI of include/hm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+
+namespace hm {
+
+typedef double2 cplx;   // complex128 as (re, im)
+
+// ----------------------------------------------------------- gather GEMM
+// A task computes one output panel of m rows x nrhs columns:
+//   acc = sum over its items of op(A_item) * in_item
+//   mode 0: out = acc        mode 1: out = base + acc
+// Panels live in "vector buffers" with row stride nrhs (RHS fastest).
+struct GTask {
+  int out_buf, out_row, m, it0, it1, base_buf, base_row, mode;
+};
+// op(A) is m x k: trans = 0 -> A[r * lda + c]; trans = 1 -> A[c * lda + r].
+struct GItem {
+  long long a_off;
+  int a_buf, lda, trans, k, in_buf, in_row;
+};
+// Finalize: out = base + sum of scratch panels (rows s of slot list).
+struct FTask {
+  int out_buf, out_row, m, base_buf, base_row, s0, s1;
+};
+
+// logical vector buffers named by tasks; bound to physical panels per launch
+enum { VB_IN = 0, VB_OUT = 1, VB_SCR = 2, VB_FAR = 3, MAX_VBUF = 4 };
+enum { MAX_ABUF = 6 };
+struct VBufs { cplx* p[MAX_VBUF]; };
+struct ABufs { const cplx* p[MAX_ABUF]; };
+// physical panels of the solve (N x nrhs unless noted)
+enum { P_B = 0, P_BO = 1, P_Y = 2, P_Z = 3, P_IT = 4, P_XT = 5, P_R = 6,
+       P_SCR = 7,   // split-K scratch (sweep scratch rows)
+       P_FAR = 8,   // far-field stage-1 panels (2 * sum of ranks rows)
+       P_HB = 9, P_HX = 10,   // staging of host-buffer solves
+       NPHYS = 11 };
+// matrix buffers
+enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3 };
+
+// A launch-ready list of tasks (device copies of the host vectors).
+struct TaskList {
+  std::vector<GTask> tasks;
+  std::vector<GItem> items;
+  GTask* d_tasks = nullptr;
+  GItem* d_items = nullptr;
+  long long flops = 0;    // complex MACs per RHS
+  long long a_bytes = 0;  // matrix bytes read per launch
+};
+struct FinList {
+  std::vector<FTask> tasks;
+  std::vector<int> slots;
+  FTask* d_tasks = nullptr;
+  int* d_slots = nullptr;
+};
+// One sweep = a sequence of levels, each a partial launch and a finalize.
+struct Sweep {
+  std::vector<TaskList> part;
+  std::vector<FinList> fin;
+  int scratch_rows = 0;   // rows of VB_SCR needed
+};
+
+struct FarDesc {
+  int kind;               // 0 low rank U V^T, 1 dense
+  int r0, m, c0, n, rank;
+  long long offU, offV;   // element offsets in the far buffer (dense: offU)
+};
+struct NearDesc { int i, j; long long off; };
+
+}  // namespace hm
+
+struct hm_ctx {
+  hm_params p;
+  int N = 0, nl = 0;
+  int dev = 0;
+  cudaStream_t stream = 0;
+  std::vector<long long> perm, leaf_off;
+  std::vector<int> m;                      // leaf sizes
+  // host copies of the structure
+  std::vector<hm::NearDesc> near;
+  std::vector<hm::FarDesc> far;
+  std::vector<std::vector<int>> rows;      // alpha pattern, rows[k] = {j > k}
+  std::vector<long long> alpha_off;        // per (k, j) in row order
+  std::vector<long long> alpha_row_start;  // index of first (k, .) in alpha_off
+  std::vector<long long> dinv_off;         // per leaf
+  double wavelength = 1.0, k = 0.0;
+  bool has_scaling = false;
+  // device data
+  int* d_perm = nullptr;
+  hm::cplx* d_near = nullptr;   long long near_elems = 0;
+  hm::cplx* d_far = nullptr;    long long far_elems = 0;
+  hm::cplx* d_alpha = nullptr;  long long alpha_elems = 0;
+  hm::cplx* d_dinv = nullptr;   long long dinv_elems = 0;
+  // host copies kept for save / rebuild (FP64 values)
+  std::vector<hm::cplx> h_near, h_far, h_alpha, h_dinv;
+  // schedules
+  hm::Sweep fwd, bwd;
+  hm::TaskList dinv_tl, far1_tl, far2_tl, near_tl;
+  int far_t_rows = 0;           // rows of VB_FAR (2 * sum rank)
+  bool sched_ready = false;
+  // work buffers sized for cap_nrhs
+  int cap_nrhs = 0;
+  hm::cplx* d_vec[hm::NPHYS] = {nullptr};
+  size_t vec_rows[hm::NPHYS] = {0};
+  int last_nrhs = 0;
+  void* mixed = nullptr;        // low-precision copies (hm_mixed.cu)
+  // mesh (hm_build handles only)
+  double* d_verts = nullptr;
+  int* d_tris = nullptr;
+  int* d_edge = nullptr;        // per RWG: tri+, tri-, free+, free-
+  std::vector<double> verts;
+  std::vector<int> tris, edge;
+  double* d_norms = nullptr;    // 4 * cap_nrhs
+  std::vector<double> ratio, resid;
+  size_t dev_bytes = 0;
+};
+
+namespace hm {
+// kernels.cu
+hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                       cudaStream_t s);
+hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s);
+hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
+                             cudaStream_t s);
+hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,
+                              cudaStream_t s);
+hm_status launch_axpby(cplx* out, const cplx* a, double sa, const cplx* b, double sb,
+                       size_t n, cudaStream_t s);
+hm_status launch_col_norms2(const cplx* V, int N, int nrhs, double* out, cudaStream_t s);
+hm_status launch_plane_wave(const double* d_verts, const int* d_tris, const int* d_edge_tri,
+                            int N, double k, const double* d_ang, int nrhs, cplx* B,
+                            cudaStream_t s);
+// api.cu helpers
+hm_status cuda_status(cudaError_t e);
+}  // namespace hm
+
+#define HM_CUDA(x)                                       \
+  do {                                                   \
+    cudaError_t _e = (x);                                \
+    if (_e != cudaSuccess) return hm::cuda_status(_e);   \
+  } while (0)

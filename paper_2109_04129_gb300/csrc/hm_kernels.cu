@@ -1,0 +1,271 @@
+// FP64 kernels of the power-series solve: one generic "gather GEMM" that
+// carries every block product of the chain (R^T and R sweeps of Eq. 25-26,
+// the block-diagonal Z~_N^-1 of Eq. 32, both stages of the low-rank far-field
+// product U (V^T y) of Eq. 11/13 and the near-field product), the split-K
+// finalize, permutations, an axpby and per-RHS column norms (Eq. 45).
+//
+// Layout: vector panels are row-major (row stride nrhs, RHS fastest), so a
+// row of a panel is one contiguous run of complex values.  Matrix blocks are
+// row-major complex128.
+#include "hm_internal.h"
+
+namespace hm {
+
+namespace {
+
+constexpr int MT = 64;    // output rows per tile
+constexpr int KT = 32;    // inner-dimension tile
+constexpr int NTHR = 256;
+
+__device__ __forceinline__ void cmac(cplx& acc, cplx a, cplx x) {
+  acc.x = fma(a.x, x.x, acc.x);
+  acc.x = fma(-a.y, x.y, acc.x);
+  acc.y = fma(a.x, x.y, acc.y);
+  acc.y = fma(a.y, x.x, acc.y);
+}
+
+// Stage the (MT x KT) tile of op(A) rows [r0, r0+MT) x cols [k0, k0+KT) into
+// shared memory, zero outside (m, k).  Both orientations read along the
+// contiguous direction of A, so global loads are coalesced.
+__device__ __forceinline__ void load_a_tile(cplx (*As)[KT + 1], const cplx* A, int lda, int trans,
+                                            int r0, int m, int k0, int k) {
+  if (!trans) {
+    for (int e = threadIdx.x; e < MT * KT; e += NTHR) {
+      int rr = e / KT, cc = e % KT;
+      int r = r0 + rr, c = k0 + cc;
+      As[rr][cc] = (r < m && c < k) ? A[(long long)r * lda + c] : make_double2(0.0, 0.0);
+    }
+  } else {
+    for (int e = threadIdx.x; e < MT * KT; e += NTHR) {
+      int cc = e / MT, rr = e % MT;
+      int r = r0 + rr, c = k0 + cc;
+      As[rr][cc] = (r < m && c < k) ? A[(long long)c * lda + r] : make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// NT = RHS columns per CTA.  NT == 1: 64 rows x 4 k-lanes, shuffle reduce.
+// NT >= 4: each thread owns RPT rows x CPT columns.
+template <int NT>
+__global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ tasks,
+                                                       const GItem* __restrict__ items,
+                                                       VBufs vb, ABufs ab, int nrhs) {
+  const GTask t = tasks[blockIdx.x];
+  const int c0 = blockIdx.y * NT;
+  __shared__ cplx As[MT][KT + 1];
+  __shared__ cplx Xs[KT][NT];
+  constexpr int CPT = (NT >= 16) ? 4 : (NT >= 4 ? NT / 4 : 1);
+  constexpr int RPT = (NT >= 4) ? NT / (4 * CPT) : 1;
+  constexpr int CG = (NT >= 4) ? NT / CPT : 1;        // column groups
+  const int tid = threadIdx.x;
+  int trow, tcol, klane;
+  if (NT == 1) {
+    trow = tid >> 2;
+    klane = tid & 3;
+    tcol = 0;
+  } else {
+    trow = (tid / CG) * RPT;
+    tcol = (tid % CG) * CPT;
+    klane = 0;
+  }
+  for (int r0 = 0; r0 < t.m; r0 += MT) {
+    cplx acc[RPT][CPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int it = t.it0; it < t.it1; ++it) {
+      const GItem I = items[it];
+      const cplx* A = ab.p[I.a_buf] + I.a_off;
+      const cplx* X = vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+      for (int k0 = 0; k0 < I.k; k0 += KT) {
+        load_a_tile(As, A, I.lda, I.trans, r0, t.m, k0, I.k);
+        for (int e = tid; e < KT * NT; e += NTHR) {
+          int kk = e / NT, cc = e % NT;
+          int kr = k0 + kk, col = c0 + cc;
+          Xs[kk][cc] = (kr < I.k && col < nrhs) ? X[(long long)kr * nrhs + col]
+                                                : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        if (NT == 1) {
+#pragma unroll 8
+          for (int kk = klane; kk < KT; kk += 4) cmac(acc[0][0], As[trow][kk], Xs[kk][0]);
+        } else {
+#pragma unroll 4
+          for (int kk = 0; kk < KT; ++kk) {
+            cplx a[RPT], x[CPT];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) a[i] = As[trow + i][kk];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) x[j] = Xs[kk][tcol + j];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+              for (int j = 0; j < CPT; ++j) cmac(acc[i][j], a[i], x[j]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (NT == 1) {
+      // lanes 4q..4q+3 hold partial sums of the same row
+      cplx v = acc[0][0];
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+      acc[0][0] = v;
+      if (klane != 0) continue;
+    }
+    cplx* out = vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+    const cplx* base = (t.mode == 1) ? vb.p[t.base_buf] + (long long)t.base_row * nrhs : nullptr;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      int r = r0 + trow + i;
+      if (r >= t.m) continue;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        int col = c0 + tcol + j;
+        if (col >= nrhs) continue;
+        cplx v = acc[i][j];
+        if (base) {
+          cplx b = base[(long long)r * nrhs + col];
+          v.x += b.x;
+          v.y += b.y;
+        }
+        out[(long long)r * nrhs + col] = v;
+      }
+    }
+  }
+}
+
+__global__ void k_finalize(const FTask* __restrict__ tasks, const int* __restrict__ slots,
+                           VBufs vb, int nrhs) {
+  const FTask t = tasks[blockIdx.x];
+  const long long n = (long long)t.m * nrhs;
+  cplx* out = vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+  const cplx* base = vb.p[t.base_buf] + (long long)t.base_row * nrhs;
+  const cplx* scr = vb.p[VB_SCR];
+  for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < n;
+       e += (long long)blockDim.x * gridDim.y) {
+    cplx v = base[e];
+    for (int s = t.s0; s < t.s1; ++s) {
+      cplx p = scr[(long long)slots[s] * nrhs + e];
+      v.x += p.x;
+      v.y += p.y;
+    }
+    out[e] = v;
+  }
+}
+
+__global__ void k_gather_perm(const cplx* __restrict__ B, cplx* __restrict__ V,
+                              const int* __restrict__ perm, int N, int nrhs) {
+  long long n = (long long)N * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / nrhs), r = (int)(e % nrhs);
+    V[e] = B[(long long)r * N + perm[i]];
+  }
+}
+
+__global__ void k_scatter_perm(const cplx* __restrict__ V, cplx* __restrict__ X,
+                               const int* __restrict__ perm, int N, int nrhs) {
+  long long n = (long long)N * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / nrhs), r = (int)(e % nrhs);
+    X[(long long)r * N + perm[i]] = V[e];
+  }
+}
+
+__global__ void k_axpby(cplx* out, const cplx* a, double sa, const cplx* b, double sb, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    cplx x = a[e], y = b[e];
+    out[e] = make_double2(sa * x.x + sb * y.x, sa * x.y + sb * y.y);
+  }
+}
+
+// Squared 2-norm of each RHS column; one CTA per column, fixed-order tree
+// reduction (deterministic).
+__global__ void k_col_norms2(const cplx* __restrict__ V, int N, int nrhs, double* out) {
+  __shared__ double red[256];
+  int r = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    cplx v = V[(long long)i * nrhs + r];
+    s = fma(v.x, v.x, fma(v.y, v.y, s));
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[r] = red[0];
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                       cudaStream_t s) {
+  if (tl.tasks.empty()) return HM_OK;
+  int nt = (int)tl.tasks.size();
+  if (nrhs == 1) {
+    k_gather_gemm<1><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+  } else if (nrhs <= 4) {
+    k_gather_gemm<4><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+  } else if (nrhs <= 8) {
+    k_gather_gemm<8><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+  } else {
+    k_gather_gemm<32><<<dim3(nt, (nrhs + 31) / 32), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb,
+                                                                   ab, nrhs);
+  }
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s) {
+  if (fl.tasks.empty()) return HM_OK;
+  int ny = nrhs >= 64 ? 8 : 1;
+  k_finalize<<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots, vb,
+                                                                  nrhs);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
+                             cudaStream_t s) {
+  k_gather_perm<<<grid_for((long long)N * nrhs), 256, 0, s>>>(B, V, perm, N, nrhs);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,
+                              cudaStream_t s) {
+  k_scatter_perm<<<grid_for((long long)N * nrhs), 256, 0, s>>>(V, X, perm, N, nrhs);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_axpby(cplx* out, const cplx* a, double sa, const cplx* b, double sb, size_t n,
+                       cudaStream_t s) {
+  k_axpby<<<grid_for((long long)n), 256, 0, s>>>(out, a, sa, b, sb, n);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_col_norms2(const cplx* V, int N, int nrhs, double* out, cudaStream_t s) {
+  k_col_norms2<<<nrhs, 256, 0, s>>>(V, N, nrhs, out);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+}  // namespace hm
