@@ -12,11 +12,12 @@ float64 pairs; every matrix row-major.
   far  x n_far:    int64 kind (0 low rank, 1 dense), r0, m, c0, n, rank;
                    kind 0: U[m * rank], V[n * rank]  (block = U V^T)
                    kind 1: B[m * n]
-  if has_scaling:
+  if has_scaling (k, j below are elimination ranks; leaf elim[k] is eliminated k-th):
     int64 n_alpha
-    per leaf k: int64 count, int64 j[count]   (the stored row of alpha)
-    alpha blocks in that order: complex128 [m_k * m_j]
-    Dinv per leaf: complex128 [m_k * m_k]
+    int64 elim[n_leaves]
+    per rank k: int64 count, int64 j[count]   (the stored row of alpha)
+    alpha blocks in that order: complex128 [m_elim[k] * m_elim[j]]
+    Dinv per rank: complex128 [m_elim[k] * m_elim[k]]
 
 Parity unpinned beyond the round trip: this is a file format, not arithmetic.
 """
@@ -54,6 +55,7 @@ def write_blocks(path, H, S=None):
                 f.write(_c(P))
         if S is not None:
             f.write(struct.pack("<q", len(S.alpha)))
+            f.write(np.asarray(S.order, dtype="<i8").tobytes())
             for k in range(S.n):
                 f.write(struct.pack("<q", len(S.rows[k])))
                 f.write(np.asarray(S.rows[k], dtype="<i8").tobytes())
@@ -103,6 +105,8 @@ def read_blocks(path):
                wavelength=wl, reading=reading)
     if has_s:
         (na,) = take("<q")
+        elim = arr("<i8", nl).tolist()
+        me = m[elim]
         rows = []
         for kk in range(nl):
             (c,) = take("<q")
@@ -110,9 +114,9 @@ def read_blocks(path):
         alpha = {}
         for kk in range(nl):
             for j in rows[kk]:
-                alpha[(kk, j)] = arr("<c16", m[kk] * m[j]).reshape(m[kk], m[j])
-        dinv = [arr("<c16", m[kk] * m[kk]).reshape(m[kk], m[kk]) for kk in range(nl)]
+                alpha[(kk, j)] = arr("<c16", me[kk] * me[j]).reshape(me[kk], me[j])
+        dinv = [arr("<c16", me[kk] * me[kk]).reshape(me[kk], me[kk]) for kk in range(nl)]
         assert len(alpha) == na
-        out.update(rows=rows, alpha=alpha, Dinv=dinv)
+        out.update(rows=rows, alpha=alpha, Dinv=dinv, elim=elim)
     assert pos == len(buf)
     return out

@@ -13,6 +13,12 @@ R = (I - E)^{-1} with E_kj = alpha_kj (k < j), so x = R x~ is the block back
 substitution x_k = x~_k + sum_{j>k} alpha_kj x_j and b~ = R^T b is the forward
 substitution b~_j = b_j + sum_{k<j} alpha_kj^T b~_k (Eq. 25-26).
 
+The elimination order is a permutation of the leaves (``order[q]`` is the
+leaf eliminated q-th); rows, alpha, D are indexed by elimination rank.  The
+default is the depth-first leaf order; nested dissection (nd_order) is the
+fill-reducing alternative (the paper uses Sloan's ordering for the same
+purpose, Sec. III-A).
+
 Readings:
   * "A" (default): the scaling considers every fill-in block (the block row of
     k reaches all leaves that elimination connects to k), so Eq. 23 holds
@@ -36,17 +42,21 @@ import numpy as np
 @dataclass
 class Scaling:
     n: int
-    rows: list           # rows[k] = sorted list of j > k with alpha_kj stored
-    alpha: dict          # (k, j) -> m_k x m_j
-    D: list              # D_k
+    rows: list           # rows[k] = sorted list of ranks j > k with alpha_kj stored
+    alpha: dict          # (k, j) -> m_k x m_j   (ranks)
+    D: list              # D_k   (rank k)
     Dinv: list           # D_k^{-1}
     reading: str
+    order: list          # order[k] = leaf eliminated k-th
 
     def entries(self, leaf_off):
-        m = np.diff(leaf_off)
+        m = np.diff(leaf_off)[self.order]
         a = sum(int(m[k] * m[j]) for (k, j) in self.alpha)
         d = int(np.sum(m * m))
         return a, d
+
+    def slices(self, leaf_off):
+        return [slice(int(leaf_off[l]), int(leaf_off[l + 1])) for l in self.order]
 
 
 def near_pattern(n, near_pairs):
@@ -80,22 +90,75 @@ def symbolic_fill_naive(n, near_pairs):
     return [sorted(r) for r in rows]
 
 
-def compute_scaling(H, reading="A"):
-    """Scaling coefficients of the H-matrix's near field (see module doc)."""
+def nd_order(tree, near_pairs, min_size=4):
+    """Geometric nested dissection of the leaf graph (near pairs = edges):
+    split the leaves at the median (ties by leaf number) of the widest axis of
+    their cell centres; the separator is the part of the first half adjacent
+    to the second; order = ND(first - separator), ND(second), separator."""
+    n = tree.n_leaves
+    adj = [set() for _ in range(n)]
+    for (i, j) in near_pairs:
+        if i != j:
+            adj[i].add(j)
+            adj[j].add(i)
+    cen = []
+    for nid in tree.leaves:
+        nd = tree.nodes[nid]
+        cen.append([(nd.ijk[a] + 0.5) / (1 << nd.level) for a in range(3)])
+    cen = np.array(cen)
+    order = []
+
+    def rec(ids):
+        if len(ids) <= min_size:
+            order.extend(sorted(ids))
+            return
+        ext = [cen[ids, a].max() - cen[ids, a].min() for a in range(3)]
+        ax = int(np.argmax(ext))        # first axis among equal extents
+        srt = sorted(ids, key=lambda i: (cen[i, ax], i))
+        h = len(srt) // 2
+        second = set(srt[h:])
+        first = srt[:h]
+        sep = sorted(i for i in first if adj[i] & second)
+        sset = set(sep)
+        rec(sorted(i for i in first if i not in sset))
+        rec(sorted(second))
+        order.extend(sep)
+
+    rec(list(range(n)))
+    return order
+
+
+def compute_scaling(H, reading="A", order=None):
+    """Scaling coefficients of the H-matrix's near field (see module doc).
+    ``order``: leaves in elimination order (default: depth-first)."""
     n = H.n_leaves
-    near_pairs = list(H.near.keys())
+    if order is None:
+        order = list(range(n))
+    order = [int(x) for x in order]
+    assert sorted(order) == list(range(n))
+    pos = {leaf: q for q, leaf in enumerate(order)}
+
+    def near_blk(a, b):          # near block between ranks a <= b, or None
+        la, lb = order[a], order[b]
+        if la <= lb:
+            blk = H.near.get((la, lb))
+            return None if blk is None else blk
+        blk = H.near.get((lb, la))
+        return None if blk is None else blk.T
+
+    near_pairs = [(pos[i], pos[j]) for (i, j) in H.near.keys()]
     if reading == "A":
         rows = symbolic_fill(n, near_pairs)
     elif reading == "B":
         rows = [sorted(r) for r in near_pattern(n, near_pairs)]
     else:
         raise ValueError(reading)
-    m = np.diff(H.leaf_off)
+    m = np.diff(H.leaf_off)[order]
     Zt = {}
     for k in range(n):
-        Zt[(k, k)] = H.near[(k, k)].copy()
+        Zt[(k, k)] = near_blk(k, k).copy()
         for j in rows[k]:
-            blk = H.near.get((k, j))
+            blk = near_blk(k, j)
             Zt[(k, j)] = blk.copy() if blk is not None else \
                 np.zeros((m[k], m[j]), np.complex128)
     alpha, D, Dinv = {}, [], []
@@ -116,14 +179,15 @@ def compute_scaling(H, reading="A"):
                 tgt += aki_T @ Zt[(k, j)]
         for j in row:
             del Zt[(k, j)]
-    return Scaling(n=n, rows=rows, alpha=alpha, D=D, Dinv=Dinv, reading=reading)
+    return Scaling(n=n, rows=rows, alpha=alpha, D=D, Dinv=Dinv, reading=reading,
+                   order=order)
 
 
 # ------------------------------------------------------------ applications
 def apply_Rt(S, leaf_off, b):
     """b~ = R^T b (Eq. 25) by forward block substitution, leaf order."""
     out = np.array(b, dtype=np.complex128, copy=True)
-    sl = [slice(int(leaf_off[i]), int(leaf_off[i + 1])) for i in range(S.n)]
+    sl = S.slices(leaf_off)
     for k in range(S.n):
         for j in S.rows[k]:
             out[sl[j]] += S.alpha[(k, j)].T @ out[sl[k]]
@@ -133,7 +197,7 @@ def apply_Rt(S, leaf_off, b):
 def apply_R(S, leaf_off, x_t):
     """x = R x~ (Eq. 26) by back block substitution, leaf order."""
     out = np.array(x_t, dtype=np.complex128, copy=True)
-    sl = [slice(int(leaf_off[i]), int(leaf_off[i + 1])) for i in range(S.n)]
+    sl = S.slices(leaf_off)
     for k in range(S.n - 1, -1, -1):
         for j in S.rows[k]:
             out[sl[k]] += S.alpha[(k, j)] @ out[sl[j]]
@@ -143,8 +207,7 @@ def apply_R(S, leaf_off, x_t):
 def apply_Dinv(S, leaf_off, v):
     """Z~_N^{-1} v, block by block (Eq. 32)."""
     out = np.empty_like(v, dtype=np.complex128)
-    for k in range(S.n):
-        s = slice(int(leaf_off[k]), int(leaf_off[k + 1]))
+    for k, s in enumerate(S.slices(leaf_off)):
         out[s] = S.Dinv[k] @ v[s]
     return out
 
@@ -153,11 +216,11 @@ def dense_R(S, leaf_off):
     """R = alpha_1 alpha_2 ... alpha_n as a dense matrix, multiplying the
     dense alpha_k of Eq. 15-16 in order (small N only; tests)."""
     N = int(leaf_off[-1])
+    sl = S.slices(leaf_off)
     R = np.eye(N, dtype=np.complex128)
     for k in range(S.n):
         Ak = np.eye(N, dtype=np.complex128)
-        sk = slice(int(leaf_off[k]), int(leaf_off[k + 1]))
         for j in S.rows[k]:
-            Ak[sk, int(leaf_off[j]):int(leaf_off[j + 1])] = S.alpha[(k, j)]
+            Ak[sl[k], sl[j]] = S.alpha[(k, j)]
         R = R @ Ak
     return R

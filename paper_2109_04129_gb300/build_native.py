@@ -4,6 +4,7 @@ paper_2109_04129_gb300/libhmps.so.  Objects go to _build/ at the repo root."""
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -32,7 +33,7 @@ def _compile(src, obj, extra):
 
 
 def build(verbose=False, extra=()):
-    bdir = os.path.join(ROOT, "_build")
+    bdir = os.path.join(ROOT, "_build", platform.machine())
     os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]

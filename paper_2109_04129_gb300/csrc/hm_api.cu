@@ -74,7 +74,8 @@ void free_sweep(Sweep& sw) {
 // writing scratch panels; the finalize adds them to the target in place.
 void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
   const int n = h->nl;
-  std::vector<std::vector<std::pair<int, long long>>> src(n);   // (source leaf, alpha index)
+  const std::vector<int>& L = h->elim;                          // rank -> leaf
+  std::vector<std::vector<std::pair<int, long long>>> src(n);   // (source rank, alpha index)
   for (int k = 0; k < n; ++k) {
     long long base = h->alpha_row_start[k];
     for (size_t q = 0; q < h->rows[k].size(); ++q) {
@@ -109,15 +110,15 @@ void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
     int scr_row = 0;
     for (int t : bylev[l]) {
       if (src[t].empty()) continue;
-      const int mt = h->m[t];
-      FTask ft{VB_OUT, (int)h->leaf_off[t], mt, VB_OUT, (int)h->leaf_off[t],
+      const int mt = h->m[L[t]];
+      FTask ft{VB_OUT, (int)h->leaf_off[L[t]], mt, VB_OUT, (int)h->leaf_off[L[t]],
                (int)fl.slots.size(), 0};
       size_t q = 0;
       while (q < src[t].size()) {
         GTask task{VB_SCR, scr_row, mt, (int)tl.items.size(), 0, 0, 0, 0};
         long long kk = 0;
-        while (q < src[t].size() && (kk == 0 || kk + h->m[src[t][q].first] <= KMAX)) {
-          int s = src[t][q].first;
+        while (q < src[t].size() && (kk == 0 || kk + h->m[L[src[t][q].first]] <= KMAX)) {
+          int s = L[src[t][q].first];
           long long ai = src[t][q].second;
           GItem it;
           it.a_off = h->alpha_off[ai];
@@ -169,9 +170,10 @@ hm_status build_schedules(hm_ctx* h) {
   if (h->has_scaling) {
     build_sweep(h, true, h->fwd);
     build_sweep(h, false, h->bwd);
-    for (int k = 0; k < n; ++k) {
+    for (int q = 0; q < n; ++q) {
+      const int k = h->elim[q];
       GTask t{VB_OUT, (int)h->leaf_off[k], h->m[k], (int)h->dinv_tl.items.size(), 0, 0, 0, 0};
-      GItem it{h->dinv_off[k], AB_DINV, h->m[k], 0, h->m[k], VB_IN, (int)h->leaf_off[k]};
+      GItem it{h->dinv_off[q], AB_DINV, h->m[k], 0, h->m[k], VB_IN, (int)h->leaf_off[k]};
       h->dinv_tl.items.push_back(it);
       t.it1 = (int)h->dinv_tl.items.size();
       h->dinv_tl.tasks.push_back(t);
@@ -508,6 +510,17 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
     }
     if (has_s) {
       long long na = r.q();
+      h->elim.resize(nl);
+      {
+        std::vector<long long> el(nl);
+        r.get(el.data(), nl);
+        std::vector<char> hit(nl, 0);
+        for (long long q = 0; q < nl; ++q) {
+          if (el[q] < 0 || el[q] >= nl || hit[el[q]]) throw std::runtime_error("elim");
+          hit[el[q]] = 1;
+          h->elim[q] = (int)el[q];
+        }
+      }
       h->rows.assign(nl, {});
       h->alpha_row_start.assign(nl + 1, 0);
       long long cnt_all = 0;
@@ -529,13 +542,13 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
       for (long long k = 0; k < nl; ++k)
         for (int j : h->rows[k]) {
           h->alpha_off.push_back((long long)h->h_alpha.size());
-          size_t cnt = (size_t)h->m[k] * h->m[j];
+          size_t cnt = (size_t)h->m[h->elim[k]] * h->m[h->elim[j]];
           h->h_alpha.resize(h->h_alpha.size() + cnt);
           r.get(h->h_alpha.data() + h->alpha_off.back(), cnt);
         }
       for (long long k = 0; k < nl; ++k) {
         h->dinv_off.push_back((long long)h->h_dinv.size());
-        size_t cnt = (size_t)h->m[k] * h->m[k];
+        size_t cnt = (size_t)h->m[h->elim[k]] * h->m[h->elim[k]];
         h->h_dinv.resize(h->h_dinv.size() + cnt);
         r.get(h->h_dinv.data() + h->dinv_off.back(), cnt);
       }
@@ -597,6 +610,10 @@ hm_status hm_save(hm_handle h, const char* path) {
   if (h->has_scaling) {
     long long na = (long long)h->alpha_off.size();
     ok = ok && put(&na, 8);
+    for (int q = 0; q < h->nl; ++q) {
+      long long e = h->elim[q];
+      ok = ok && put(&e, 8);
+    }
     for (int k = 0; k < h->nl; ++k) {
       long long c = (long long)h->rows[k].size();
       ok = ok && put(&c, 8);
@@ -609,9 +626,10 @@ hm_status hm_save(hm_handle h, const char* path) {
     for (int k = 0; k < h->nl; ++k)
       for (int j : h->rows[k])
         ok = ok && put(h->h_alpha.data() + h->alpha_off[q++],
-                       (size_t)h->m[k] * h->m[j] * sizeof(cplx));
+                       (size_t)h->m[h->elim[k]] * h->m[h->elim[j]] * sizeof(cplx));
     for (int k = 0; k < h->nl; ++k)
-      ok = ok && put(h->h_dinv.data() + h->dinv_off[k], (size_t)h->m[k] * h->m[k] * sizeof(cplx));
+      ok = ok && put(h->h_dinv.data() + h->dinv_off[k],
+                     (size_t)h->m[h->elim[k]] * h->m[h->elim[k]] * sizeof(cplx));
   }
   ok = (fclose(f) == 0) && ok;
   return ok ? HM_OK : HM_ERR_IO;
@@ -759,7 +777,7 @@ hm_status hm_get_stats(hm_handle h, long long* out, int n) {
     maxr = std::max<long long>(maxr, d.rank);
   }
   for (int k = 0; k < (int)h->rows.size(); ++k)
-    for (int j : h->rows[k]) a_e += (long long)h->m[k] * h->m[j];
+    for (int j : h->rows[k]) a_e += (long long)h->m[h->elim[k]] * h->m[h->elim[j]];
   for (int k = 0; k < h->nl; ++k) d_e += (long long)h->m[k] * h->m[k];
   long long v[12] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
                      near_e, far_e, maxr, (long long)h->fwd.part.size(),
@@ -787,6 +805,13 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_verts);
   cudaFree(h->d_tris);
   cudaFree(h->d_edge);
+  cudaFree(h->mesh_q);
+  cudaFree(h->mesh_area);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->mesh_tri[i]);
+    cudaFree(h->mesh_fv[i]);
+  }
+  cudaFree(h->mesh_len);
   delete h;
   return HM_OK;
 }

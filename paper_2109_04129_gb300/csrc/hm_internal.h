@@ -86,10 +86,13 @@ struct hm_ctx {
   // host copies of the structure
   std::vector<hm::NearDesc> near;
   std::vector<hm::FarDesc> far;
-  std::vector<std::vector<int>> rows;      // alpha pattern, rows[k] = {j > k}
+  // scaling, indexed by elimination rank q (leaf elim[q] is eliminated q-th)
+  std::vector<int> elim;                   // rank -> leaf
+  std::vector<std::vector<int>> rows;      // alpha pattern, rows[q] = {ranks > q}
   std::vector<long long> alpha_off;        // per (k, j) in row order
   std::vector<long long> alpha_row_start;  // index of first (k, .) in alpha_off
-  std::vector<long long> dinv_off;         // per leaf
+  std::vector<long long> dinv_off;         // per rank
+  std::vector<double> leaf_cen;            // leaf cell centres (built handles)
   double wavelength = 1.0, k = 0.0;
   bool has_scaling = false;
   // device data
@@ -114,7 +117,12 @@ struct hm_ctx {
   // mesh (hm_build handles only)
   double* d_verts = nullptr;
   int* d_tris = nullptr;
-  int* d_edge = nullptr;        // per RWG: tri+, tri-, free+, free-
+  int* d_edge = nullptr;
+  double* mesh_q = nullptr;     // nt x 7 x 3 quadrature points
+  double* mesh_area = nullptr;
+  int* mesh_tri[2] = {nullptr, nullptr};
+  int* mesh_fv[2] = {nullptr, nullptr};
+  double* mesh_len = nullptr;
   std::vector<double> verts;
   std::vector<int> tris, edge;
   double* d_norms = nullptr;    // 4 * cap_nrhs

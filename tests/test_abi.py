@@ -19,8 +19,8 @@ def _declared():
 def lib():
     so = os.path.join(ROOT, "paper_2109_04129_gb300", "libhmps.so")
     if not os.path.exists(so):
-        from paper_2109_04129_gb300 import build_native
-        build_native.build()
+        import __graft_entry__
+        __graft_entry__.build()
     return ctypes.CDLL(so)
 
 

@@ -1,0 +1,154 @@
+"""Native set-up on the GPU against the oracle: octree / leaf order (exact),
+near blocks (<= 1e-10 relative), far blocks (approximation error against the
+EFIE entries), plane-wave RHS, Schur-complement scaling (<= 1e-9) and the
+whole pipeline build -> scaling -> solve."""
+import os
+
+import numpy as np
+import pytest
+
+import hm_workloads as hw
+from oracle.efie import EFIE
+from oracle.export import read_blocks
+from oracle.octree import Octree
+from oracle.scaling import compute_scaling, nd_order
+from oracle.series import series_solve
+from oracle.rwg import build_rwg
+from tests.oracle_cases import case
+from tests.gpu_util import load_case, to_dev, from_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+MESHES = {
+    "sphere_r0.25_L2": (lambda: hw.icosphere(2, 0.25), 32),
+    "plate_2l": (lambda: hw.plate(2.0, 20), 32),
+    "sphere_r0.5_L3": (lambda: hw.icosphere(3, 0.5), 64),
+}
+
+
+def _native(name, tmp_path, **kw):
+    import paper_2109_04129_gb300 as hp
+    mk, leaf = MESHES[name]
+    v, f = mk()
+    sol = hp.Solver.build(v, f, leaf_max=leaf, **kw)
+    return sol, v, f, leaf
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_native_tree_and_near_blocks(name, tmp_path):
+    sol, v, f, leaf = _native(name, tmp_path)
+    _, H, _, _ = case(name)
+    perm, off = sol.tree()
+    assert np.array_equal(perm, H.perm) and np.array_equal(off, H.leaf_off)
+    p = str(tmp_path / "b.hmps")
+    sol.save(p)
+    d = read_blocks(p)
+    assert sorted(d["near"]) == sorted(H.near)
+    scale = max(np.abs(b).max() for b in H.near.values())
+    worst = max(np.abs(d["near"][k] - H.near[k]).max() for k in H.near) / scale
+    assert worst < 1e-10, worst
+    # far block structure identical; each block within the ACA bound
+    assert [x[:5] for x in d["far"]] == [x[:5] for x in H.far]
+    E = EFIE(H.rwg)
+    for kind, r0, m, c0, n, P, Q in d["far"][:: max(1, len(d["far"]) // 25)]:
+        exact = E.block(H.perm[r0:r0 + m], H.perm[c0:c0 + n])
+        approx = P @ Q.T if kind == "lr" else P
+        assert np.linalg.norm(approx - exact) <= 3e-4 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("name", ["sphere_r0.25_L2", "plate_2l"])
+def test_native_plane_wave(name, tmp_path):
+    import torch
+    sol, v, f, leaf = _native(name, tmp_path)
+    w, H, _, B = case(name)
+    th, ph, po = w.angles()
+    Bd = torch.empty((len(th), sol.N), dtype=torch.complex128, device="cuda")
+    sol.plane_wave(Bd, th, ph, po)
+    assert rel(from_dev(Bd), B).max() < 1e-12
+
+
+@pytest.mark.parametrize("reading", ["A", "B"])
+@pytest.mark.parametrize("name", ["sphere_r0.25_L2", "plate_2l", "sphere_r0.5_L3"])
+def test_gpu_scaling_matches_oracle(name, reading, tmp_path):
+    import paper_2109_04129_gb300 as hp
+    w, H, _, B = case(name)
+    S = compute_scaling(H, reading)
+    sol = load_case(H, None, fill=hp.HM_FILL_FULL if reading == "A" else hp.HM_FILL_NEAR)
+    sol.compute_scaling()
+    p = str(tmp_path / "s.hmps")
+    sol.save(p)
+    d = read_blocks(p)
+    assert d["rows"] == S.rows and d["elim"] == list(range(H.n_leaves))
+    sa = max(np.abs(a).max() for a in S.alpha.values())
+    ea = max((np.abs(d["alpha"][k] - S.alpha[k]).max() for k in S.alpha), default=0.0) / sa
+    sd = max(np.abs(a).max() for a in S.Dinv)
+    ed = max(np.abs(a - b).max() for a, b in zip(d["Dinv"], S.Dinv)) / sd
+    assert ea < 1e-9 and ed < 1e-9, (ea, ed)
+
+
+def test_native_nd_order_matches_oracle(tmp_path):
+    import paper_2109_04129_gb300 as hp
+    sol, v, f, leaf = _native("sphere_r0.5_L3", tmp_path, ordering=hp.HM_ORDER_ND)
+    sol.compute_scaling()
+    p = str(tmp_path / "nd.hmps")
+    sol.save(p)
+    d = read_blocks(p)
+    _, H, S, B = case("sphere_r0.5_L3")
+    order = nd_order(H.tree, list(H.near.keys()))
+    assert d["elim"] == order
+
+
+@pytest.mark.parametrize("name", ["sphere_r0.25_L2", "sphere_r0.5_L3"])
+def test_native_pipeline_solution(name, tmp_path):
+    """build -> scaling -> RHS -> solve on the GPU vs the oracle's own build."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    for ordering in (hp.HM_ORDER_DFS, hp.HM_ORDER_ND):
+        sol, v, f, leaf = _native(name, tmp_path, ordering=ordering)
+        sol.compute_scaling()
+        w, H, S, B = case(name)
+        th, ph, po = w.angles()
+        Bd = torch.empty((len(th), sol.N), dtype=torch.complex128, device="cuda")
+        sol.plane_wave(Bd, th, ph, po)
+        X = torch.empty_like(Bd)
+        sol.solve(X, Bd)
+        want, _ = series_solve(H, S, B, 2)
+        err = rel(from_dev(X), want)
+        # independent builds: ACA factors agree to rounding unless a pivot tie
+        # flips; reading A makes x independent of the elimination order
+        assert err.max() < 1e-6, (ordering, err.max())
+
+
+def test_build_rejects_bad_meshes():
+    import paper_2109_04129_gb300 as hp
+    v, f = hw.icosphere(1, 1.0)
+    bad = f.copy()
+    bad[0, 0] = len(v) + 5
+    with pytest.raises(hp.HMError) as e:
+        hp.Solver.build(v, bad)
+    assert e.value.status == hp.HM_ERR_INVALID
+    # a non-manifold edge: three triangles on one edge
+    v2 = np.vstack([v, [[0.0, 0.0, 2.0]]])
+    f2 = np.vstack([f, [[f[0, 0], f[0, 1], len(v)]]])
+    with pytest.raises(hp.HMError) as e:
+        hp.Solver.build(v2, f2)
+    assert e.value.status == hp.HM_ERR_INVALID
+    # zero-area triangle
+    v3 = v.copy()
+    f3 = f.copy()
+    v3[f3[0, 2]] = 0.5 * (v3[f3[0, 0]] + v3[f3[0, 1]])
+    with pytest.raises(hp.HMError):
+        hp.Solver.build(v3, f3)
+
+
+def test_singular_diagonal_block_reported():
+    import paper_2109_04129_gb300 as hp
+    w, H, S, B = case("sphere_r0.25_L2")
+    import copy
+    H2 = copy.copy(H)
+    H2.near = dict(H.near)
+    H2.near[(0, 0)] = np.zeros_like(H.near[(0, 0)])
+    sol = load_case(H2, None)
+    with pytest.raises(hp.HMError) as e:
+        sol.compute_scaling()
+    assert e.value.status == hp.HM_ERR_SINGULAR

@@ -194,3 +194,22 @@ def test_two_term_error_reported_config1():
     err = float(rel_err(x2, x_lu)[0])
     print(f"two-term error vs LU {err:.3f}, ratio {float(ratio[0, 0]):.3f}")
     assert np.isfinite(err) and ratio.shape == (1, 1)
+
+
+def test_nested_dissection_order_same_solution():
+    """Reading A makes x = Z_N^-1 b - Z_N^-1 Z_F Z_N^-1 b independent of the
+    elimination order (R D^-1 R^T = Z_N^-1); nested dissection reduces fill."""
+    from oracle.scaling import nd_order
+    w, H, S, B = case("sphere_r0.5_L3")
+    order = nd_order(H.tree, list(H.near.keys()))
+    assert sorted(order) == list(range(H.n_leaves))
+    S2 = compute_scaling(H, "A", order)
+    x1, r1 = series_solve(H, S, B, 2)
+    x2, r2 = series_solve(H, S2, B, 2)
+    assert np.all(rel_err(x2, x1) < 1e-11)
+    assert S2.entries(H.leaf_off)[0] < S.entries(H.leaf_off)[0]
+    ZN = _dense_near(H)
+    R = dense_R(S2, H.leaf_off)
+    M = R.T @ ZN @ R
+    for k, sk in enumerate(S2.slices(H.leaf_off)):
+        assert np.allclose(M[sk, sk], S2.D[k], atol=1e-11 * np.abs(M).max())
