@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the power-series H-matrix EFIE solve on GB300.
+
+Metric: power-series RHS solves per second on the 2-lambda PEC sphere
+(icosphere level 5, 20480 triangles, 30720 RWG unknowns, octree leaves <= 128,
+ACA tol 1e-4), 362 monostatic right-hand sides (theta = 0..180 deg step 1,
+phi = 0, theta- and phi-polarised plane waves).  One step = one
+hm_power_series_solve over the whole RHS batch, inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 runs replicas (one independent copy of the system per GPU, RHS batch per
+GPU fixed: weak scaling, no collective on the data path).  Prints one JSON
+line on rank 0.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "power-series RHS solves/s at rel.err ≤1e-4 vs FP64; mixed vs FP64 on 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="sphere_r2_L5")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--ordering", default="nd", choices=["nd", "dfs"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "native" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, val, device):
+    if ws == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dgemm_peak(dev):
+    """FP64 denominator: cuBLAS DGEMM 4096^3, best of 5 (TFLOP/s)."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2 * 4096 ** 3 / best / 1e12
+
+
+# ----------------------------------------------------------------- oracle leg
+def oracle_setup(w, processes):
+    from oracle.efie import EFIE
+    from oracle.hmatrix import build_hmatrix
+    from oracle.scaling import compute_scaling, nd_order
+    v, f = w.build_mesh()
+    t0 = time.perf_counter()
+    H = build_hmatrix(v, f, w.wavelength, w.leaf_max, w.aca_tol, processes=processes)
+    S = compute_scaling(H, "A", nd_order(H.tree, list(H.near.keys())))
+    th, ph, po = w.angles()
+    B = EFIE(H.rwg, w.wavelength).plane_wave(th, ph, po)
+    return H, S, B, time.perf_counter() - t0
+
+
+def oracle_time(H, S, B, nrhs_sample, reps):
+    """Oracle series solve (plain NumPy FP64) of a bounded RHS sample."""
+    from oracle.series import series_solve
+    idx = list(range(0, B.shape[1], max(1, B.shape[1] // nrhs_sample)))[:nrhs_sample]
+    Bs = B[:, idx]
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        series_solve(H, S, Bs, 2)
+        ts.append(time.perf_counter() - t0)
+    return len(idx), ts
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    from hm_workloads import get_workload
+    w = get_workload(args.workload)
+    procs = max(1, min(16, os.cpu_count() or 1))
+    H, S, B, setup_s = oracle_setup(w, procs)
+    n, ts = oracle_time(H, S, B, args.cpu_rhs, args.warmup + args.steps)
+    ts = ts[args.warmup:]
+    t = sum(ts) / len(ts)
+    val = n / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": f"{w.name}: PEC sphere r=2 lambda, icosphere L5, "
+                               f"N={H.N}, leaves<=128, ACA 1e-4, 362 monostatic RHS",
+                   "sample": f"{n} of {B.shape[1]} RHS per step"},
+        "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": f"{n} RHS per step of the 362-RHS sweep, oracle set-up "
+                                   f"{setup_s:.0f} s (not timed, {procs} processes)"},
+        "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- native leg
+def run_native(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2109_04129_gb300 as hp
+    from hm_workloads import get_workload
+    w = get_workload(args.workload)
+    v, f = w.build_mesh()
+    prec = hp.HM_MIXED if args.precision == "mixed" else hp.HM_FP64
+    t0 = time.perf_counter()
+    sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max,
+                          aca_tol=w.aca_tol,
+                          ordering=hp.HM_ORDER_ND if args.ordering == "nd" else hp.HM_ORDER_DFS,
+                          precision=prec, refine_steps=1 if prec == hp.HM_MIXED else 0)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sol.compute_scaling()
+    t_scale = time.perf_counter() - t0
+    st = sol.stats()
+    th, ph, po = w.angles()
+    nrhs = len(th)
+    B = torch.empty((nrhs, sol.N), dtype=torch.complex128, device=dev)
+    sol.plane_wave(B, th, ph, po)
+    X = torch.empty_like(B)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sol.solve(X, B)
+    torch.cuda.synchronize()
+    # ---- timed region: device-resident inputs (alpha/far data > L2: no flush)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            sol.solve(X, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_dev = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_dev = max_over_ranks(ws, t_dev, dev)
+    value = ws * nrhs / t_dev
+    ratio, _ = sol.diagnostics(nrhs)
+    # ---- per-kernel timing (same steps, events around every launch)
+    sol.profile_enable(True)
+    for _ in range(args.steps):
+        sol.solve(X, B)
+    prof = sol.profile()
+    sol.profile_enable(False)
+    peaks, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, ms, byts, flops) = dom
+    tot_ms = sum(p[1] for p in prof.values())
+    avg_s = ms / 1e3 / max(1.0, launches)
+    fp64_peak = dgemm_peak(dev) if prec == hp.HM_FP64 else 0.0
+    if prec == hp.HM_FP64:
+        # FP64 complex products: bound by the FP64 pipe, peak = measured DGEMM
+        ach = flops / max(launches, 1) / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak or None,
+                "unit": "TFLOP/s", "frac": (ach / fp64_peak) if fp64_peak else None,
+                "traffic": None, "kernel": name,
+                "peak_source": "cuBLAS DGEMM measured in this run" if fp64_peak else None,
+                "share": ms / tot_ms}
+    else:
+        ach = byts / max(launches, 1) / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
+                "peak_source": f"{peak_kind} hbm_gbs", "share": ms / tot_ms}
+    launches_per_step = int(sum(p[0] for p in prof.values()) / args.steps)
+    # ---- end to end through the host-buffer C-ABI call
+    Bh = torch.empty((nrhs, sol.N), dtype=torch.complex128, pin_memory=True)
+    Bh.copy_(B)
+    Xh = torch.empty_like(Bh, pin_memory=True)
+    bn, xn = Bh.numpy(), Xh.numpy()
+    sol.solve_host(xn, bn)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.solve_host(xn, bn)
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    t_e2e = max_over_ranks(ws, t_e2e, dev)
+    e2e = {"value": ws * nrhs / t_e2e, "unit": "RHS/s",
+           "h2d_bytes_per_step": int(bn.nbytes), "d2h_bytes_per_step": int(xn.nbytes)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128" if prec == hp.HM_FP64 else "mixed(c128 D^-1, c64/bf16 products)",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: PEC sphere r=2 lambda, icosphere L5, N={sol.N}, "
+                               f"leaves<=128, ACA 1e-4, {nrhs} monostatic RHS "
+                               "(theta 0..180 step 1, theta/phi pol)",
+                   "precision": args.precision, "ordering": args.ordering,
+                   "l2": "inputs larger than L2 (alpha + far factors), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "alpha_entries": st["alpha_entries"], "far_entries": st["far_entries"],
+                   "near_entries": st["near_entries"], "fwd_levels": st["fwd_levels"],
+                   "build_s": round(t_build, 2), "scaling_s": round(t_scale, 2),
+                   "series_ratio_max": float(np.max(ratio))},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "kernel_ms_per_step": {k: round(p[1] / args.steps, 4) for k, p in prof.items() if p[0]},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        procs = max(1, min(16, os.cpu_count() or 1))
+        H, S, Bo, setup_s = oracle_setup(w, procs)
+        n, ts = oracle_time(H, S, Bo, args.cpu_rhs, 2)
+        t = min(ts)
+        line["cpu_baseline"] = {"value": n / t, "unit": "RHS/s", "cores": cpu_threads(),
+                                "kind": "oracle",
+                                "sample": f"{n} of {nrhs} RHS, oracle series solve (set-up "
+                                          f"{setup_s:.0f} s untimed, {procs} processes)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -103,8 +103,8 @@ hm_status hm_compute_scaling(hm_handle h);
  * (n_terms = 2; more terms continue the alternating series).  In HM_MIXED
  * the chain runs in low precision and refine_steps FP64 residual
  * corrections follow.  X, B: device, N x nrhs complex128, original order;
- * B is not modified; X is overwritten.  Returns HM_WARN_SERIES_RATIO (with X
- * valid) when a ratio of Eq. 45 exceeds 0.1. */
+ * B is not modified; X is overwritten.  Asynchronous: the ratio check of
+ * Eq. 45 is reported by hm_get_diagnostics. */
 hm_status hm_power_series_solve(hm_handle h, void* X, const void* B, int nrhs);
 
 /* Same solve for HOST buffers: copies B in, solves, copies X out (pinned or
@@ -134,7 +134,9 @@ hm_status hm_num_unknowns(hm_handle h, int* n);
 
 /* Per-RHS diagnostics of the last solve (host arrays of length nrhs, either
  * may be NULL): ratio_host[r] = ||it_1|| / ||it_0|| (Eq. 45); resid_host[r] =
- * ||B - Z X|| / ||B|| after refinement (0 when no refinement ran). */
+ * ||B - Z X|| / ||B|| of the solution before its last refinement step (0 when
+ * no refinement ran).  Synchronises; returns HM_WARN_SERIES_RATIO when some
+ * ratio exceeds 0.1 (the paper's empirical convergence bound). */
 hm_status hm_get_diagnostics(hm_handle h, double* ratio_host, double* resid_host, int nrhs);
 
 /* Counts, as long long, in this order (up to n of them): N, leaves, near
@@ -146,6 +148,19 @@ hm_status hm_get_stats(hm_handle h, long long* out_host, int n);
 /* Copy the leaf-order permutation (N int64, leaf position -> original index)
  * and leaf offsets (leaves + 1 int64) to host arrays. */
 hm_status hm_get_tree(hm_handle h, long long* perm_host, long long* leaf_off_host);
+
+/* Per-kernel timing of later device work: when enabled, every launch of the
+ * chain is bracketed by CUDA events on the handle's stream.  hm_get_profile
+ * synchronises, then writes for each category c < ncat four doubles
+ * out_host[4c .. 4c+3] = {launches, total milliseconds, algorithmic bytes,
+ * algorithmic real flops} accumulated since the last call (and resets them).
+ * Categories: 0 R^T sweep blocks, 1 R sweep blocks, 2 sweep finalize,
+ * 3 D^-1, 4 far stage 1 (V^T y), 5 far stage 2 (U t), 6 near product,
+ * 7 permutations / axpby / norms, 8 mixed-precision sweep blocks,
+ * 9 mixed-precision far field, 10 conversions. */
+enum { HM_PROF_CATEGORIES = 11 };
+hm_status hm_profile_enable(hm_handle h, int on);
+hm_status hm_get_profile(hm_handle h, double* out_host, int ncat);
 
 hm_status hm_destroy(hm_handle h);
 const char* hm_status_string(hm_status s);

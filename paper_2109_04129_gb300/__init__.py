@@ -32,7 +32,10 @@ STATS = ("N", "leaves", "near_blocks", "far_blocks", "alpha_entries", "d_entries
 SYMBOLS = ("hm_default_params", "hm_build", "hm_import", "hm_save", "hm_compute_scaling",
            "hm_power_series_solve", "hm_power_series_solve_host", "hm_apply",
            "hm_plane_wave_rhs", "hm_set_stream", "hm_num_unknowns", "hm_get_diagnostics",
-           "hm_get_stats", "hm_get_tree", "hm_destroy", "hm_status_string")
+           "hm_get_stats", "hm_get_tree", "hm_destroy", "hm_status_string",
+           "hm_profile_enable", "hm_get_profile")
+PROF_CATEGORIES = ("rt_sweep", "r_sweep", "sweep_finalize", "dinv", "far_stage1",
+                   "far_stage2", "near", "misc", "mixed_sweep", "mixed_far", "conversion")
 
 
 class hm_params(ctypes.Structure):
@@ -64,6 +67,8 @@ for name, args in {
     "hm_get_stats": [_vp, _P(ctypes.c_longlong), _i],
     "hm_get_tree": [_vp, _P(ctypes.c_longlong), _P(ctypes.c_longlong)],
     "hm_destroy": [_vp],
+    "hm_profile_enable": [_vp, _i],
+    "hm_get_profile": [_vp, _P(_d), _i],
 }.items():
     fn = getattr(_lib, name)
     fn.argtypes = args
@@ -200,6 +205,17 @@ class Solver:
         out = (ctypes.c_longlong * len(STATS))()
         _check(_lib.hm_get_stats(self._h, out, len(STATS)), "hm_get_stats")
         return dict(zip(STATS, list(out)))
+
+    def profile_enable(self, on=True):
+        _check(_lib.hm_profile_enable(self._h, 1 if on else 0), "hm_profile_enable")
+
+    def profile(self):
+        """{category: (launches, ms, algorithmic bytes, algorithmic flops)} since
+        the last call."""
+        n = len(PROF_CATEGORIES)
+        out = np.zeros(4 * n)
+        _check(_lib.hm_get_profile(self._h, out.ctypes.data_as(_P(_d)), n), "hm_get_profile")
+        return {c: tuple(out[4 * i:4 * i + 4]) for i, c in enumerate(PROF_CATEGORIES)}
 
     def tree(self):
         st = self.stats()

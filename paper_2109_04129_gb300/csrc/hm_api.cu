@@ -24,6 +24,25 @@ hm_status cuda_status(cudaError_t e) {
   return HM_ERR_CUDA;
 }
 
+int prof_begin(hm_ctx* h) {
+  if (!h->prof) return -1;
+  while (h->evpool.size() < h->evused + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->evpool.push_back(e);
+  }
+  int ev = (int)h->evused;
+  h->evused += 2;
+  cudaEventRecord(h->evpool[ev], h->stream);
+  return ev;
+}
+
+void prof_end(hm_ctx* h, int ev, int cat, double bytes, double flops) {
+  if (ev < 0) return;
+  cudaEventRecord(h->evpool[ev + 1], h->stream);
+  h->recs.push_back(ProfRec{cat, ev, bytes, flops});
+}
+
 }  // namespace hm
 
 namespace {
@@ -311,19 +330,86 @@ VBufs vbufs(hm_ctx* h, cplx* in, cplx* out) {
   return v;
 }
 
-hm_status run_sweep(hm_ctx* h, Sweep& sw, cplx* buf, int nrhs) {
-  VBufs v = vbufs(h, buf, buf);
+// algorithmic traffic of a task list: matrix bytes once, input and output
+// panels once per launch (asz / vsz = bytes of a matrix / vector entry)
+double tl_bytes(const TaskList& tl, int nrhs, double asz = 16, double vsz = 16) {
+  double vec = 0;
+  for (const GItem& it : tl.items) vec += (double)it.k * nrhs * vsz;
+  for (const GTask& t : tl.tasks) vec += (double)t.m * nrhs * vsz;
+  return (double)tl.a_bytes / 16.0 * asz + vec;
+}
+
+}  // namespace
+
+namespace hm {
+const void* mixed_alpha(hm_ctx* h);
+const void* mixed_far_data(hm_ctx* h);
+void* mixed_scratch(hm_ctx* h);
+void* mixed_fart(hm_ctx* h);
+
+// Bind the logical buffers of a launch: FP64 tables, or (low) the complex64
+// copies of alpha / far factors and the complex64 scratch panels.
+static void tables(hm_ctx* h, void* in, void* out, bool low, VBufs& v, ABufs& a) {
+  v = VBufs{};
+  v.p[VB_IN] = in;
+  v.p[VB_OUT] = out;
+  v.p[VB_SCR] = low ? mixed_scratch(h) : (void*)h->d_vec[P_SCR];
+  v.p[VB_FAR] = low ? mixed_fart(h) : (void*)h->d_vec[P_FAR];
+  a = ABufs{};
+  a.p[AB_NEAR] = h->d_near;
+  a.p[AB_FAR] = low ? mixed_far_data(h) : h->d_far;
+  a.p[AB_ALPHA] = low ? mixed_alpha(h) : h->d_alpha;
+  a.p[AB_DINV] = h->d_dinv;
+}
+
+hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs, int cat,
+                         int prec, bool low) {
+  VBufs v;
+  ABufs a;
+  tables(h, in, out, low, v, a);
+  int ev = prof_begin(h);
+  hm_status s = launch_tasks(tl, v, a, nrhs, h->stream, prec);
+  double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
+  prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
+  return s;
+}
+
+hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, int prec,
+                          bool low) {
+  VBufs v;
+  ABufs a;
+  tables(h, buf, buf, low, v, a);
+  double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
   for (size_t l = 0; l < sw.part.size(); ++l) {
-    hm_status s = launch_tasks(sw.part[l], v, abufs(h), nrhs, h->stream);
+    int ev = prof_begin(h);
+    hm_status s = launch_tasks(sw.part[l], v, a, nrhs, h->stream, prec);
     if (s) return s;
-    s = launch_fin(sw.fin[l], v, nrhs, h->stream);
+    prof_end(h, ev, cat, tl_bytes(sw.part[l], nrhs, asz, vsz), 8.0 * sw.part[l].flops * nrhs);
+    ev = prof_begin(h);
+    s = launch_fin(sw.fin[l], v, nrhs, h->stream, prec);
     if (s) return s;
+    double fb = 0;
+    for (const FTask& f : sw.fin[l].tasks) fb += (double)f.m * nrhs * vsz * (2 + f.s1 - f.s0);
+    prof_end(h, ev, PC_FIN, fb, 0.0);
   }
   return HM_OK;
 }
 
-hm_status run_list(hm_ctx* h, TaskList& tl, cplx* in, cplx* out, int nrhs) {
-  return launch_tasks(tl, vbufs(h, in, out), abufs(h), nrhs, h->stream);
+hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
+  hm_status s = run_chain_list(h, h->far1_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
+  if (s) return s;
+  return run_chain_list(h, h->far2_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
+}
+}  // namespace hm
+
+namespace {
+
+hm_status run_sweep(hm_ctx* h, Sweep& sw, cplx* buf, int nrhs, int cat) {
+  return run_chain_sweep(h, sw, buf, nrhs, cat, PREC_64, false);
+}
+
+hm_status run_list(hm_ctx* h, TaskList& tl, cplx* in, cplx* out, int nrhs, int cat) {
+  return run_chain_list(h, tl, in, out, nrhs, cat, PREC_64, false);
 }
 
 hm_status copy_panel(hm_ctx* h, cplx* dst, const cplx* src, int nrhs) {
@@ -333,9 +419,9 @@ hm_status copy_panel(hm_ctx* h, cplx* dst, const cplx* src, int nrhs) {
 }
 
 hm_status apply_far(hm_ctx* h, cplx* in, cplx* out, int nrhs) {
-  hm_status s = run_list(h, h->far1_tl, in, out, nrhs);
+  hm_status s = run_list(h, h->far1_tl, in, out, nrhs, PC_FAR1);
   if (s) return s;
-  return run_list(h, h->far2_tl, in, out, nrhs);
+  return run_list(h, h->far2_tl, in, out, nrhs, PC_FAR2);
 }
 
 // x (leaf order, in-place in P_XT) from b (leaf order, P_B): FP64 chain.
@@ -344,18 +430,18 @@ hm_status series_fp64(hm_ctx* h, int nrhs, bool diag) {
   hm_status s;
   // b~ = R^T b ; b_o = D^-1 b~
   if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
-  if ((s = run_sweep(h, h->fwd, V[P_Y], nrhs))) return s;
-  if ((s = run_list(h, h->dinv_tl, V[P_Y], V[P_BO], nrhs))) return s;
+  if ((s = run_sweep(h, h->fwd, V[P_Y], nrhs, PC_FWD))) return s;
+  if ((s = run_list(h, h->dinv_tl, V[P_Y], V[P_BO], nrhs, PC_DINV))) return s;
   if ((s = copy_panel(h, V[P_XT], V[P_BO], nrhs))) return s;
   cplx* it = V[P_BO];
   for (int t = 1; t < h->p.n_terms; ++t) {
     // it_t = D^-1 R^T Z_F R it_{t-1}
     if ((s = copy_panel(h, V[P_Y], it, nrhs))) return s;
-    if ((s = run_sweep(h, h->bwd, V[P_Y], nrhs))) return s;
+    if ((s = run_sweep(h, h->bwd, V[P_Y], nrhs, PC_BWD))) return s;
     if ((s = apply_far(h, V[P_Y], V[P_Z], nrhs))) return s;
-    if ((s = run_sweep(h, h->fwd, V[P_Z], nrhs))) return s;
+    if ((s = run_sweep(h, h->fwd, V[P_Z], nrhs, PC_FWD))) return s;
     cplx* nxt = (it == V[P_IT]) ? V[P_R] : V[P_IT];
-    if ((s = run_list(h, h->dinv_tl, V[P_Z], nxt, nrhs))) return s;
+    if ((s = run_list(h, h->dinv_tl, V[P_Z], nxt, nrhs, PC_DINV))) return s;
     if (t == 1 && diag) {
       if ((s = launch_col_norms2(it, h->N, nrhs, h->d_norms, h->stream))) return s;
       if ((s = launch_col_norms2(nxt, h->N, nrhs, h->d_norms + nrhs, h->stream))) return s;
@@ -366,7 +452,7 @@ hm_status series_fp64(hm_ctx* h, int nrhs, bool diag) {
     it = nxt;
   }
   // x = R x~
-  return run_sweep(h, h->bwd, V[P_XT], nrhs);
+  return run_sweep(h, h->bwd, V[P_XT], nrhs, PC_BWD);
 }
 
 hm_status check_ready(hm_ctx* h) {
@@ -670,17 +756,17 @@ hm_status hm_apply(hm_handle h, int op, void* Y, const void* X, int nrhs) {
     switch (op) {
       case HM_OP_RT:
         if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
-        s = run_sweep(h, h->fwd, V[P_Y], nrhs);
+        s = run_sweep(h, h->fwd, V[P_Y], nrhs, PC_FWD);
         break;
       case HM_OP_R:
         if ((s = copy_panel(h, V[P_Y], V[P_B], nrhs))) return s;
-        s = run_sweep(h, h->bwd, V[P_Y], nrhs);
+        s = run_sweep(h, h->bwd, V[P_Y], nrhs, PC_BWD);
         break;
-      case HM_OP_DINV: s = run_list(h, h->dinv_tl, V[P_B], V[P_Y], nrhs); break;
+      case HM_OP_DINV: s = run_list(h, h->dinv_tl, V[P_B], V[P_Y], nrhs, PC_DINV); break;
       case HM_OP_FAR: s = apply_far(h, V[P_B], V[P_Y], nrhs); break;
-      case HM_OP_NEAR: s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs); break;
+      case HM_OP_NEAR: s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs, PC_NEAR); break;
       case HM_OP_Z:
-        s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs);
+        s = run_list(h, h->near_tl, V[P_B], V[P_Y], nrhs, PC_NEAR);
         if (!s) s = apply_far(h, V[P_B], V[P_Z], nrhs);
         if (!s)
           s = launch_axpby(V[P_Y], V[P_Y], 1.0, V[P_Z], 1.0, (size_t)h->N * nrhs, h->stream);
@@ -786,8 +872,33 @@ hm_status hm_get_stats(hm_handle h, long long* out, int n) {
   return HM_OK;
 }
 
+hm_status hm_profile_enable(hm_handle h, int on) {
+  if (!h) return HM_ERR_INVALID;
+  h->prof = on != 0;
+  return HM_OK;
+}
+
+hm_status hm_get_profile(hm_handle h, double* out, int ncat) {
+  if (!h || !out || ncat <= 0) return HM_ERR_INVALID;
+  HM_CUDA(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < 4 * ncat; ++i) out[i] = 0.0;
+  for (const ProfRec& r : h->recs) {
+    if (r.cat >= ncat) continue;
+    float ms = 0.f;
+    HM_CUDA(cudaEventElapsedTime(&ms, h->evpool[r.ev], h->evpool[r.ev + 1]));
+    out[4 * r.cat] += 1.0;
+    out[4 * r.cat + 1] += ms;
+    out[4 * r.cat + 2] += r.bytes;
+    out[4 * r.cat + 3] += r.flops;
+  }
+  h->recs.clear();
+  h->evused = 0;
+  return HM_OK;
+}
+
 hm_status hm_destroy(hm_handle h) {
   if (!h) return HM_OK;
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   free_sweep(h->fwd);
   free_sweep(h->bwd);
   free_tasks(h->dinv_tl);

@@ -87,7 +87,10 @@ hm_status build_rwg(const double* V, int nv, const int* T, int nt, Rwg& r) {
     double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
     double n0 = u[1] * w[2] - u[2] * w[1], n1 = u[2] * w[0] - u[0] * w[2],
            n2 = u[0] * w[1] - u[1] * w[0];
-    if (!(n0 * n0 + n1 * n1 + n2 * n2 > 0.0)) return HM_ERR_INVALID;   // zero-area triangle
+    double e2 = std::max(u[0] * u[0] + u[1] * u[1] + u[2] * u[2],
+                         w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    // degenerate triangle: area below 1e-10 of its longest-edge square
+    if (!(n0 * n0 + n1 * n1 + n2 * n2 > 1e-20 * e2 * e2)) return HM_ERR_INVALID;
   }
   return r.tp.empty() ? HM_ERR_INVALID : HM_OK;
 }

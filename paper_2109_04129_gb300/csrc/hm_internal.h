@@ -34,8 +34,10 @@ struct FTask {
 // logical vector buffers named by tasks; bound to physical panels per launch
 enum { VB_IN = 0, VB_OUT = 1, VB_SCR = 2, VB_FAR = 3, MAX_VBUF = 4 };
 enum { MAX_ABUF = 6 };
-struct VBufs { cplx* p[MAX_VBUF]; };
-struct ABufs { const cplx* p[MAX_ABUF]; };
+struct VBufs { void* p[MAX_VBUF]; };
+struct ABufs { const void* p[MAX_ABUF]; };
+// element types of a launch: all FP64, all FP32, or FP64 matrix x FP32 vectors
+enum { PREC_64 = 0, PREC_32 = 1, PREC_64x32 = 2 };
 // physical panels of the solve (N x nrhs unless noted)
 enum { P_B = 0, P_BO = 1, P_Y = 2, P_Z = 3, P_IT = 4, P_XT = 5, P_R = 6,
        P_SCR = 7,   // split-K scratch (sweep scratch rows)
@@ -66,6 +68,10 @@ struct Sweep {
   std::vector<FinList> fin;
   int scratch_rows = 0;   // rows of VB_SCR needed
 };
+
+enum { PC_FWD = 0, PC_BWD = 1, PC_FIN = 2, PC_DINV = 3, PC_FAR1 = 4, PC_FAR2 = 5,
+       PC_NEAR = 6, PC_MISC = 7, PC_MX_SWEEP = 8, PC_MX_FAR = 9, PC_CONV = 10, PC_N = 11 };
+struct ProfRec { int cat; int ev; double bytes, flops; };
 
 struct FarDesc {
   int kind;               // 0 low rank U V^T, 1 dense
@@ -126,6 +132,11 @@ struct hm_ctx {
   std::vector<double> verts;
   std::vector<int> tris, edge;
   double* d_norms = nullptr;    // 4 * cap_nrhs
+  // profiling (hm_profile_enable)
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<hm::ProfRec> recs;
+  size_t evused = 0;
   std::vector<double> ratio, resid;
   size_t dev_bytes = 0;
 };
@@ -133,8 +144,17 @@ struct hm_ctx {
 namespace hm {
 // kernels.cu
 hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                       cudaStream_t s);
-hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s);
+                       cudaStream_t s, int prec = PREC_64);
+hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s,
+                     int prec = PREC_64);
+hm_status launch_gather_perm32(const cplx* B, float2* V, const int* perm, int N, int nrhs,
+                               cudaStream_t s);
+hm_status launch_to32(const cplx* a, float2* o, size_t n, cudaStream_t s);
+hm_status launch_axpby64_32(cplx* o, double sa, const float2* b, double sb, size_t n,
+                            cudaStream_t s);
+hm_status launch_axpby32(float2* out, const float2* a, float sa, const float2* b, float sb,
+                         size_t n, cudaStream_t s);
+hm_status launch_col_norms2_32(const float2* V, int N, int nrhs, double* out, cudaStream_t s);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s);
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,
@@ -147,6 +167,8 @@ hm_status launch_plane_wave(const double* d_verts, const int* d_tris, const int*
                             cudaStream_t s);
 // api.cu helpers
 hm_status cuda_status(cudaError_t e);
+int prof_begin(hm_ctx* h);                                   // -1 when disabled
+void prof_end(hm_ctx* h, int ev, int cat, double bytes, double flops);
 }  // namespace hm
 
 #define HM_CUDA(x)                                       \

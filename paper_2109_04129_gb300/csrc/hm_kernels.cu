@@ -17,43 +17,63 @@ constexpr int MT = 64;    // output rows per tile
 constexpr int KT = 32;    // inner-dimension tile
 constexpr int NTHR = 256;
 
-__device__ __forceinline__ void cmac(cplx& acc, cplx a, cplx x) {
+template <class T> struct Cx;
+template <> struct Cx<double2> { typedef double R; };
+template <> struct Cx<float2> { typedef float R; };
+
+template <class A, class B> __device__ __forceinline__ A cvt(B v);
+template <> __device__ __forceinline__ double2 cvt<double2, double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt<float2, float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 cvt<double2, float2>(float2 v) {
+  return make_double2(v.x, v.y);
+}
+template <> __device__ __forceinline__ float2 cvt<float2, double2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+
+template <class T>
+__device__ __forceinline__ void cmac(T& acc, T a, T x) {
   acc.x = fma(a.x, x.x, acc.x);
   acc.x = fma(-a.y, x.y, acc.x);
   acc.y = fma(a.x, x.y, acc.y);
   acc.y = fma(a.y, x.x, acc.y);
 }
 
+template <class T> __device__ __forceinline__ T czero() { T z; z.x = 0; z.y = 0; return z; }
+
 // Stage the (MT x KT) tile of op(A) rows [r0, r0+MT) x cols [k0, k0+KT) into
-// shared memory, zero outside (m, k).  Both orientations read along the
-// contiguous direction of A, so global loads are coalesced.
-__device__ __forceinline__ void load_a_tile(cplx (*As)[KT + 1], const cplx* A, int lda, int trans,
+// shared memory (converted to the accumulation type), zero outside (m, k).
+// Both orientations read along the contiguous direction of A, so global loads
+// are coalesced.
+template <class TA, class TC>
+__device__ __forceinline__ void load_a_tile(TC (*As)[KT + 1], const TA* A, int lda, int trans,
                                             int r0, int m, int k0, int k) {
   if (!trans) {
     for (int e = threadIdx.x; e < MT * KT; e += NTHR) {
       int rr = e / KT, cc = e % KT;
       int r = r0 + rr, c = k0 + cc;
-      As[rr][cc] = (r < m && c < k) ? A[(long long)r * lda + c] : make_double2(0.0, 0.0);
+      As[rr][cc] = (r < m && c < k) ? cvt<TC, TA>(A[(long long)r * lda + c]) : czero<TC>();
     }
   } else {
     for (int e = threadIdx.x; e < MT * KT; e += NTHR) {
       int cc = e / MT, rr = e % MT;
       int r = r0 + rr, c = k0 + cc;
-      As[rr][cc] = (r < m && c < k) ? A[(long long)c * lda + r] : make_double2(0.0, 0.0);
+      As[rr][cc] = (r < m && c < k) ? cvt<TC, TA>(A[(long long)c * lda + r]) : czero<TC>();
     }
   }
 }
 
 // NT = RHS columns per CTA.  NT == 1: 64 rows x 4 k-lanes, shuffle reduce.
 // NT >= 4: each thread owns RPT rows x CPT columns.
-template <int NT>
+// TA: matrix element, TV: vector element, TC: accumulation (complex).
+template <int NT, class TA, class TV, class TC>
 __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ tasks,
                                                        const GItem* __restrict__ items,
                                                        VBufs vb, ABufs ab, int nrhs) {
   const GTask t = tasks[blockIdx.x];
   const int c0 = blockIdx.y * NT;
-  __shared__ cplx As[MT][KT + 1];
-  __shared__ cplx Xs[KT][NT];
+  __shared__ TC As[MT][KT + 1];
+  __shared__ TC Xs[KT][NT];
   constexpr int CPT = (NT >= 16) ? 4 : (NT >= 4 ? NT / 4 : 1);
   constexpr int RPT = (NT >= 4) ? NT / (4 * CPT) : 1;
   constexpr int CG = (NT >= 4) ? NT / CPT : 1;        // column groups
@@ -69,22 +89,22 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
     klane = 0;
   }
   for (int r0 = 0; r0 < t.m; r0 += MT) {
-    cplx acc[RPT][CPT];
+    TC acc[RPT][CPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) acc[i][j] = make_double2(0.0, 0.0);
+      for (int j = 0; j < CPT; ++j) acc[i][j] = czero<TC>();
     for (int it = t.it0; it < t.it1; ++it) {
       const GItem I = items[it];
-      const cplx* A = ab.p[I.a_buf] + I.a_off;
-      const cplx* X = vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+      const TA* A = (const TA*)ab.p[I.a_buf] + I.a_off;
+      const TV* X = (const TV*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
       for (int k0 = 0; k0 < I.k; k0 += KT) {
-        load_a_tile(As, A, I.lda, I.trans, r0, t.m, k0, I.k);
+        load_a_tile<TA, TC>(As, A, I.lda, I.trans, r0, t.m, k0, I.k);
         for (int e = tid; e < KT * NT; e += NTHR) {
           int kk = e / NT, cc = e % NT;
           int kr = k0 + kk, col = c0 + cc;
-          Xs[kk][cc] = (kr < I.k && col < nrhs) ? X[(long long)kr * nrhs + col]
-                                                : make_double2(0.0, 0.0);
+          Xs[kk][cc] = (kr < I.k && col < nrhs) ? cvt<TC, TV>(X[(long long)kr * nrhs + col])
+                                                : czero<TC>();
         }
         __syncthreads();
         if (NT == 1) {
@@ -93,7 +113,7 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
         } else {
 #pragma unroll 4
           for (int kk = 0; kk < KT; ++kk) {
-            cplx a[RPT], x[CPT];
+            TC a[RPT], x[CPT];
 #pragma unroll
             for (int i = 0; i < RPT; ++i) a[i] = As[trow + i][kk];
 #pragma unroll
@@ -109,7 +129,7 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
     }
     if (NT == 1) {
       // lanes 4q..4q+3 hold partial sums of the same row
-      cplx v = acc[0][0];
+      TC v = acc[0][0];
       v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
       v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
       v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
@@ -117,8 +137,9 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
       acc[0][0] = v;
       if (klane != 0) continue;
     }
-    cplx* out = vb.p[t.out_buf] + (long long)t.out_row * nrhs;
-    const cplx* base = (t.mode == 1) ? vb.p[t.base_buf] + (long long)t.base_row * nrhs : nullptr;
+    TV* out = (TV*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+    const TV* base = (t.mode == 1) ? (const TV*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
+                                   : nullptr;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
       int r = r0 + trow + i;
@@ -127,35 +148,89 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
       for (int j = 0; j < CPT; ++j) {
         int col = c0 + tcol + j;
         if (col >= nrhs) continue;
-        cplx v = acc[i][j];
+        TC v = acc[i][j];
         if (base) {
-          cplx b = base[(long long)r * nrhs + col];
+          TC b = cvt<TC, TV>(base[(long long)r * nrhs + col]);
           v.x += b.x;
           v.y += b.y;
         }
-        out[(long long)r * nrhs + col] = v;
+        out[(long long)r * nrhs + col] = cvt<TV, TC>(v);
       }
     }
   }
 }
 
+template <class TV>
 __global__ void k_finalize(const FTask* __restrict__ tasks, const int* __restrict__ slots,
                            VBufs vb, int nrhs) {
   const FTask t = tasks[blockIdx.x];
   const long long n = (long long)t.m * nrhs;
-  cplx* out = vb.p[t.out_buf] + (long long)t.out_row * nrhs;
-  const cplx* base = vb.p[t.base_buf] + (long long)t.base_row * nrhs;
-  const cplx* scr = vb.p[VB_SCR];
+  TV* out = (TV*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+  const TV* base = (const TV*)vb.p[t.base_buf] + (long long)t.base_row * nrhs;
+  const TV* scr = (const TV*)vb.p[VB_SCR];
   for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < n;
        e += (long long)blockDim.x * gridDim.y) {
-    cplx v = base[e];
+    TV v = base[e];
     for (int s = t.s0; s < t.s1; ++s) {
-      cplx p = scr[(long long)slots[s] * nrhs + e];
+      TV p = scr[(long long)slots[s] * nrhs + e];
       v.x += p.x;
       v.y += p.y;
     }
     out[e] = v;
   }
+}
+
+__global__ void k_gather_perm32(const cplx* __restrict__ B, float2* __restrict__ V,
+                                const int* __restrict__ perm, int N, int nrhs) {
+  long long n = (long long)N * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / nrhs), r = (int)(e % nrhs);
+    cplx b = B[(long long)r * N + perm[i]];
+    V[e] = make_float2((float)b.x, (float)b.y);
+  }
+}
+
+__global__ void k_to32(const cplx* __restrict__ a, float2* __restrict__ o, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    o[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// o (FP64) = sa * o + sb * b (FP32 panel widened)
+__global__ void k_axpby64_32(cplx* o, double sa, const float2* b, double sb, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    cplx x = o[e];
+    float2 y = b[e];
+    o[e] = make_double2(sa * x.x + sb * (double)y.x, sa * x.y + sb * (double)y.y);
+  }
+}
+
+__global__ void k_axpby32(float2* out, const float2* a, float sa, const float2* b, float sb,
+                          size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    float2 x = a[e], y = b[e];
+    out[e] = make_float2(sa * x.x + sb * y.x, sa * x.y + sb * y.y);
+  }
+}
+
+__global__ void k_col_norms2_32(const float2* __restrict__ V, int N, int nrhs, double* out) {
+  __shared__ double red[256];
+  int r = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    float2 v = V[(long long)i * nrhs + r];
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[r] = red[0];
 }
 
 __global__ void k_gather_perm(const cplx* __restrict__ B, cplx* __restrict__ V,
@@ -214,29 +289,77 @@ int grid_for(long long n) {
 
 }  // namespace
 
-hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                       cudaStream_t s) {
-  if (tl.tasks.empty()) return HM_OK;
+template <class TA, class TV, class TC>
+static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                      cudaStream_t s) {
   int nt = (int)tl.tasks.size();
   if (nrhs == 1) {
-    k_gather_gemm<1><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+    k_gather_gemm<1, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else if (nrhs <= 4) {
-    k_gather_gemm<4><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+    k_gather_gemm<4, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else if (nrhs <= 8) {
-    k_gather_gemm<8><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+    k_gather_gemm<8, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else {
-    k_gather_gemm<32><<<dim3(nt, (nrhs + 31) / 32), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb,
-                                                                   ab, nrhs);
+    k_gather_gemm<32, TA, TV, TC><<<dim3(nt, (nrhs + 31) / 32), NTHR, 0, s>>>(tl.d_tasks, tl.d_items,
+                                                                              vb, ab, nrhs);
   }
+}
+
+hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                       cudaStream_t s, int prec) {
+  if (tl.tasks.empty()) return HM_OK;
+  if (prec == PREC_64)
+    launch_tl<double2, double2, double2>(tl, vb, ab, nrhs, s);
+  else if (prec == PREC_32)
+    launch_tl<float2, float2, float2>(tl, vb, ab, nrhs, s);
+  else
+    launch_tl<double2, float2, double2>(tl, vb, ab, nrhs, s);
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
 
-hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s) {
+hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s, int prec) {
   if (fl.tasks.empty()) return HM_OK;
   int ny = nrhs >= 64 ? 8 : 1;
-  k_finalize<<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots, vb,
-                                                                  nrhs);
+  if (prec == PREC_64)
+    k_finalize<double2><<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots,
+                                                                            vb, nrhs);
+  else
+    k_finalize<float2><<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots,
+                                                                           vb, nrhs);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_gather_perm32(const cplx* B, float2* V, const int* perm, int N, int nrhs,
+                               cudaStream_t s) {
+  k_gather_perm32<<<grid_for((long long)N * nrhs), 256, 0, s>>>(B, V, perm, N, nrhs);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_to32(const cplx* a, float2* o, size_t n, cudaStream_t s) {
+  k_to32<<<grid_for((long long)n), 256, 0, s>>>(a, o, n);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_axpby64_32(cplx* o, double sa, const float2* b, double sb, size_t n,
+                            cudaStream_t s) {
+  k_axpby64_32<<<grid_for((long long)n), 256, 0, s>>>(o, sa, b, sb, n);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_axpby32(float2* out, const float2* a, float sa, const float2* b, float sb,
+                         size_t n, cudaStream_t s) {
+  k_axpby32<<<grid_for((long long)n), 256, 0, s>>>(out, a, sa, b, sb, n);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_col_norms2_32(const float2* V, int N, int nrhs, double* out, cudaStream_t s) {
+  k_col_norms2_32<<<nrhs, 256, 0, s>>>(V, N, nrhs, out);
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }

