@@ -162,6 +162,24 @@ enum { HM_PROF_CATEGORIES = 11 };
 hm_status hm_profile_enable(hm_handle h, int on);
 hm_status hm_get_profile(hm_handle h, double* out_host, int ncat);
 
+/* Far-field product that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the product (code inside a pre-sized pool or
+ * arena that owns the device memory, a framework allocator that forbids raw
+ * cudaMalloc, latency-critical loops).  It computes Y = Z_F X like hm_apply
+ * with HM_OP_FAR (FP64 factors, original RWG order, column-major N x nrhs
+ * complex128 device buffers owned by the caller) but calls no cudaMalloc,
+ * cudaFree or allocating library routine: its only scratch, 2 * (sum of the
+ * far-block ranks) * nrhs complex128 values, lives in a fixed file-scope
+ * device array of HM_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  Returns HM_ERR_INVALID when that scratch
+ * would exceed the array (reduce nrhs).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Asynchronous on the handle's stream.  All calls
+ * share the array: calls whose kernels overlap on the GPU race. */
+#define HM_NOALLOC_SCRATCH_BYTES (32u << 20)
+hm_status hm_apply_far_noalloc(hm_handle h, void* Y, const void* X, int nrhs);
+
 hm_status hm_destroy(hm_handle h);
 const char* hm_status_string(hm_status s);
 

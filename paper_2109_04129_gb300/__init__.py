@@ -33,7 +33,7 @@ SYMBOLS = ("hm_default_params", "hm_build", "hm_import", "hm_save", "hm_compute_
            "hm_power_series_solve", "hm_power_series_solve_host", "hm_apply",
            "hm_plane_wave_rhs", "hm_set_stream", "hm_num_unknowns", "hm_get_diagnostics",
            "hm_get_stats", "hm_get_tree", "hm_destroy", "hm_status_string",
-           "hm_profile_enable", "hm_get_profile")
+           "hm_profile_enable", "hm_get_profile", "hm_apply_far_noalloc")
 PROF_CATEGORIES = ("rt_sweep", "r_sweep", "sweep_finalize", "dinv", "far_stage1",
                    "far_stage2", "near", "misc", "mixed_sweep", "mixed_far", "conversion")
 
@@ -69,6 +69,7 @@ for name, args in {
     "hm_destroy": [_vp],
     "hm_profile_enable": [_vp, _i],
     "hm_get_profile": [_vp, _P(_d), _i],
+    "hm_apply_far_noalloc": [_vp, _vp, _vp, _i],
 }.items():
     fn = getattr(_lib, name)
     fn.argtypes = args
@@ -182,6 +183,14 @@ class Solver:
         self._panel_ok(Y, self.N)
         self._stream()
         _check(_lib.hm_apply(self._h, OPS[op], _ptr(Y), _ptr(X), X.shape[0]), "hm_apply")
+
+    def apply_far_noalloc(self, Y, X):
+        """Y = Z_F X without any device allocation (fixed library scratch)."""
+        self._panel_ok(X, self.N)
+        self._panel_ok(Y, self.N)
+        self._stream()
+        _check(_lib.hm_apply_far_noalloc(self._h, _ptr(Y), _ptr(X), X.shape[0]),
+               "hm_apply_far_noalloc")
 
     def plane_wave(self, B, theta, phi, pol):
         self._panel_ok(B, self.N)
