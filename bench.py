@@ -135,11 +135,11 @@ def max_over_ranks(ws, val, device):
     return float(t.item())
 
 
-def dgemm_peak(dev):
-    """FP64 denominator: cuBLAS DGEMM 4096^3, best of 5 (TFLOP/s)."""
+def gemm_peak(dev, dtype):
+    """ALU denominators: cuBLAS GEMM 4096^3 in the given dtype, best of 5 (TFLOP/s)."""
     import torch
-    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
-    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    a = torch.randn(4096, 4096, dtype=dtype, device=dev)
+    b = torch.randn(4096, 4096, dtype=dtype, device=dev)
     a @ b
     torch.cuda.synchronize()
     best = 1e30
@@ -161,7 +161,8 @@ def oracle_setup(w, processes):
     from oracle.scaling import compute_scaling, nd_order
     v, f = w.build_mesh()
     t0 = time.perf_counter()
-    H = build_hmatrix(v, f, w.wavelength, w.leaf_max, w.aca_tol, processes=processes)
+    H = build_hmatrix(v, f, w.wavelength, w.leaf_max, w.aca_tol, processes=processes,
+                      use_c=True)
     S = compute_scaling(H, "A", nd_order(H.tree, list(H.near.keys())))
     th, ph, po = w.angles()
     B = EFIE(H.rwg, w.wavelength).plane_wave(th, ph, po)
@@ -179,6 +180,31 @@ def oracle_time(H, S, B, nrhs_sample, reps):
         series_solve(H, S, Bs, 2)
         ts.append(time.perf_counter() - t0)
     return len(idx), ts
+
+
+def oracle_job(name, processes, nrhs_sample, reps, conn):
+    """Oracle set-up and timed sample in a separate (spawned) process; the
+    result goes back through a pipe."""
+    try:
+        from hm_workloads import get_workload
+        w = get_workload(name)
+        H, S, B, setup_s = oracle_setup(w, processes)
+        n, ts = oracle_time(H, S, B, nrhs_sample, reps)
+        conn.send({"n": n, "ts": ts, "setup_s": setup_s, "threads": cpu_threads(),
+                   "nrhs": B.shape[1]})
+    except Exception as e:  # reported in the JSON line
+        conn.send({"error": repr(e)})
+    conn.close()
+
+
+def start_oracle(name, nrhs_sample, reps):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    parent, child = ctx.Pipe(duplex=False)
+    procs = max(1, min(16, (os.cpu_count() or 2) - 2))
+    p = ctx.Process(target=oracle_job, args=(name, procs, nrhs_sample, reps, child))
+    p.start()
+    return p, parent, procs
 
 
 def cpu_threads():
@@ -220,9 +246,14 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- native leg
 def run_native(args):
+    ws, rank, local = dist_setup(args)
+    # the oracle leg starts before the first GPU call (spawned, CPU only) and
+    # runs while the GPU is measured
+    oracle = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        oracle = start_oracle(args.workload, args.cpu_rhs, 2)
     import numpy as np
     import torch
-    ws, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2109_04129_gb300 as hp
@@ -255,11 +286,13 @@ def run_native(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("hm_timed")
         e0.record(stream)
         for _ in range(args.steps):
             sol.solve(X, B)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     barrier(ws)
     t_dev = e0.elapsed_time(e1) / 1e3 / args.steps
     t_dev = max_over_ranks(ws, t_dev, dev)
@@ -272,18 +305,27 @@ def run_native(args):
     prof = sol.profile()
     sol.profile_enable(False)
     peaks, peak_kind = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (launches, ms, byts, flops) = dom
+    fp64_peak = gemm_peak(dev, torch.float64)
+    fp32_peak = gemm_peak(dev, torch.float32)
+    fp32_cats = {"mixed_sweep", "mixed_far"}
     tot_ms = sum(p[1] for p in prof.values())
+    kernels = {}
+    for cat, (launches, ms, byts, flops) in prof.items():
+        if not launches:
+            continue
+        kernels[cat] = {"ms_per_step": round(ms / args.steps, 3), "share": round(ms / tot_ms, 4),
+                        "launches_per_step": int(launches / args.steps),
+                        "tflops": round(flops / (ms / 1e3) / 1e12, 4),
+                        "gbs": round(byts / (ms / 1e3) / 1e9, 2)}
+    name, (launches, ms, byts, flops) = max(prof.items(), key=lambda kv: kv[1][1])
     avg_s = ms / 1e3 / max(1.0, launches)
-    fp64_peak = dgemm_peak(dev) if prec == hp.HM_FP64 else 0.0
-    if prec == hp.HM_FP64:
-        # FP64 complex products: bound by the FP64 pipe, peak = measured DGEMM
+    if flops > 0:
+        pk = fp32_peak if name in fp32_cats else fp64_peak
         ach = flops / max(launches, 1) / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak or None,
-                "unit": "TFLOP/s", "frac": (ach / fp64_peak) if fp64_peak else None,
+        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": None, "kernel": name,
-                "peak_source": "cuBLAS DGEMM measured in this run" if fp64_peak else None,
+                "peak_source": ("cuBLAS SGEMM" if name in fp32_cats else "cuBLAS DGEMM")
+                               + " 4096^3 measured in this run",
                 "share": ms / tot_ms}
     else:
         ach = byts / max(launches, 1) / avg_s / 1e9
@@ -325,17 +367,24 @@ def run_native(args):
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
-        "kernel_ms_per_step": {k: round(p[1] / args.steps, 4) for k, p in prof.items() if p[0]},
+        "kernels": kernels,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        procs = max(1, min(16, os.cpu_count() or 1))
-        H, S, Bo, setup_s = oracle_setup(w, procs)
-        n, ts = oracle_time(H, S, Bo, args.cpu_rhs, 2)
-        t = min(ts)
-        line["cpu_baseline"] = {"value": n / t, "unit": "RHS/s", "cores": cpu_threads(),
-                                "kind": "oracle",
-                                "sample": f"{n} of {nrhs} RHS, oracle series solve (set-up "
-                                          f"{setup_s:.0f} s untimed, {procs} processes)"}
+    if oracle is not None:
+        proc, conn, procs = oracle
+        res = conn.recv()
+        proc.join()
+        if "error" in res:
+            line["cpu_baseline"] = {"value": None, "unit": "RHS/s", "kind": "oracle",
+                                    "error": res["error"]}
+        else:
+            t = min(res["ts"])
+            line["cpu_baseline"] = {
+                "value": res["n"] / t, "unit": "RHS/s", "cores": res["threads"],
+                "kind": "oracle",
+                "sample": f"{res['n']} of {res['nrhs']} RHS of the same sweep, oracle FP64 "
+                          f"series solve (NumPy), best of 2; oracle set-up "
+                          f"{res['setup_s']:.0f} s untimed ({procs} processes, during the GPU "
+                          "measurement)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -97,14 +97,20 @@ class HMatrix:
 _W = {}
 
 
-def _worker_init(verts, tris, wavelength):
+def _worker_init(verts, tris, wavelength, use_c=False):
     rwg = build_rwg(verts, tris)
-    _W["efie"] = EFIE(rwg, wavelength)
+    E = EFIE(rwg, wavelength)
+    _W["efie"] = E
+    if use_c:
+        from .cefie import CBlock
+        _W["block"] = CBlock(E)          # same entries, plain C (oracle/cefie.c)
+    else:
+        _W["block"] = E.block
 
 
 def _near_task(args):
     rows, cols, diag = args
-    Bk = _W["efie"].block(rows, cols)
+    Bk = _W["block"](rows, cols)
     if diag:
         Bk = 0.5 * (Bk + Bk.T)
     return Bk
@@ -112,21 +118,23 @@ def _near_task(args):
 
 def _far_task(args):
     rows, cols, eps = args
-    E = _W["efie"]
-    U, V = aca(lambda i: E.block(rows[i:i + 1], cols)[0],
-               lambda j: E.block(rows, cols[j:j + 1])[:, 0],
+    blk = _W["block"]
+    U, V = aca(lambda i: blk(rows[i:i + 1], cols)[0],
+               lambda j: blk(rows, cols[j:j + 1])[:, 0],
                len(rows), len(cols), eps)
     U, V = recompress(U, V, eps)
     m, n = len(rows), len(cols)
     if U.shape[1] * (m + n) >= m * n:
-        return ("dense", E.block(rows, cols), None)
+        return ("dense", blk(rows, cols), None)
     return ("lr", U, V)
 
 
 def build_hmatrix(verts, tris, wavelength=1.0, leaf_max=64, aca_tol=1e-4,
-                  processes=None):
+                  processes=None, use_c=False):
     """Fill the H-matrix of a mesh.  ``processes`` > 1 runs the block fills in
-    a spawn-started process pool (same arithmetic, block by block)."""
+    a spawn-started process pool (same arithmetic, block by block);
+    ``use_c`` evaluates the entries with the plain-C statement of the same
+    formulas (oracle/cefie.c) instead of NumPy."""
     rwg = build_rwg(verts, tris)
     tree = Octree(rwg.centre, leaf_max)
     near_u, far_u = tree.upper_blocks()
@@ -146,12 +154,28 @@ def build_hmatrix(verts, tris, wavelength=1.0, leaf_max=64, aca_tol=1e-4,
     if processes > 1:
         import multiprocessing as mp
         ctx = mp.get_context("spawn")
-        with ctx.Pool(processes, initializer=_worker_init,
-                      initargs=(np.asarray(verts), np.asarray(tris), wavelength)) as pool:
-            near_res = pool.map(_near_task, near_jobs, chunksize=16)
-            far_res = pool.map(_far_task, far_jobs, chunksize=16)
+        if use_c:
+            from .cefie import build as _build_c
+            _build_c()
+        # one BLAS thread per worker process (the pool already fills the cores)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            with ctx.Pool(processes, initializer=_worker_init,
+                          initargs=(np.asarray(verts), np.asarray(tris), wavelength,
+                                    use_c)) as pool:
+                near_res = pool.map(_near_task, near_jobs, chunksize=16)
+                far_res = pool.map(_far_task, far_jobs, chunksize=16)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
     else:
-        _worker_init(verts, tris, wavelength)
+        _worker_init(verts, tris, wavelength, use_c)
         near_res = [_near_task(a) for a in near_jobs]
         far_res = [_far_task(a) for a in far_jobs]
     near = {key: Bk for key, Bk in zip(near_u, near_res)}

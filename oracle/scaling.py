@@ -168,15 +168,22 @@ def compute_scaling(H, reading="A", order=None):
         D.append(Dk)
         Dinv.append(Dk_inv)
         row = rows[k]
-        for j in row:
-            alpha[(k, j)] = -Dk_inv @ Zt[(k, j)]
+        if not row:
+            continue
+        # the block row k as one panel [Z~_kj, j in row]: alpha row = -D_k^-1 panel
+        # (Eq. 16); all Schur updates alpha_ki^T Z~_kj as one panel product (Eq. 21)
+        cuts = np.concatenate([[0], np.cumsum([m[j] for j in row])])
+        panel = np.concatenate([Zt[(k, j)] for j in row], axis=1)
+        apanel = -Dk_inv @ panel
+        upd = apanel.T @ panel
         for a, i in enumerate(row):
-            aki_T = alpha[(k, i)].T
-            for j in row[a:]:
-                tgt = Zt.get((i, j))
+            alpha[(k, i)] = apanel[:, cuts[a]:cuts[a + 1]]
+        for a, i in enumerate(row):
+            for b in range(a, len(row)):
+                tgt = Zt.get((i, row[b]))
                 if tgt is None:
                     continue                      # reading B: outside the pattern
-                tgt += aki_T @ Zt[(k, j)]
+                tgt += upd[cuts[a]:cuts[a + 1], cuts[b]:cuts[b + 1]]
         for j in row:
             del Zt[(k, j)]
     return Scaling(n=n, rows=rows, alpha=alpha, D=D, Dinv=Dinv, reading=reading,

@@ -47,7 +47,8 @@ void prof_end(hm_ctx* h, int ev, int cat, double bytes, double flops) {
 
 namespace {
 
-const long long KMAX = 512;   // inner rows per split-K task of a sweep
+const long long KMAX = 128;   // inner rows per split-K task of a sweep (more CTAs on
+                              // the narrow top levels of the elimination tree)
 
 template <class T>
 hm_status upload(T** dptr, const std::vector<T>& v, size_t* bytes) {

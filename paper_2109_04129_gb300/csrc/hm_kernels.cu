@@ -160,6 +160,86 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
   }
 }
 
+// Many-RHS variant: one CTA owns up to 128 rows of a target panel and a
+// 32-column RHS slice.  Lane = RHS column, warp = row group (rows g, g+8, ...),
+// so the inner dimension streams without row-tile padding: per inner index a
+// column of op(A) (broadcast from shared memory) meets one row of the input
+// panel (one value per lane).
+constexpr int RK = 16;     // inner rows per staged chunk
+constexpr int RR = 128;    // rows per pass
+template <class TA, class TV, class TC>
+__global__ void __launch_bounds__(256) k_gather_rows(const GTask* __restrict__ tasks,
+                                                     const GItem* __restrict__ items, VBufs vb,
+                                                     ABufs ab, int nrhs) {
+  const GTask t = tasks[blockIdx.x];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  __shared__ TC As[RK][RR + 1];
+  __shared__ TC Xs[RK][32];
+  constexpr int RPT = RR / 8;
+  for (int r0 = 0; r0 < t.m; r0 += RR) {
+    const int mr = min(RR, t.m - r0);
+    TC acc[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i] = czero<TC>();
+    for (int it = t.it0; it < t.it1; ++it) {
+      const GItem I = items[it];
+      const TA* A = (const TA*)ab.p[I.a_buf] + I.a_off;
+      const TV* X = (const TV*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+      for (int k0 = 0; k0 < I.k; k0 += RK) {
+        const int kc = min(RK, I.k - k0);
+        if (!I.trans) {
+          for (int e = threadIdx.x; e < RR * RK; e += 256) {
+            int r = e / RK, kk = e % RK;
+            As[kk][r] = (r < mr && kk < kc) ? cvt<TC, TA>(A[(long long)(r0 + r) * I.lda + k0 + kk])
+                                            : czero<TC>();
+          }
+        } else {
+          for (int e = threadIdx.x; e < RR * RK; e += 256) {
+            int kk = e / RR, r = e % RR;
+            As[kk][r] = (r < mr && kk < kc) ? cvt<TC, TA>(A[(long long)(k0 + kk) * I.lda + r0 + r])
+                                            : czero<TC>();
+          }
+        }
+        for (int e = threadIdx.x; e < RK * 32; e += 256) {
+          int kk = e >> 5, c = e & 31;
+          int cc = blockIdx.y * 32 + c;
+          Xs[kk][c] = (kk < kc && cc < nrhs) ? cvt<TC, TV>(X[(long long)(k0 + kk) * nrhs + cc])
+                                             : czero<TC>();
+        }
+        __syncthreads();
+        // rows g, g+8, ... below mr only (warp-uniform bound: no divergence)
+        const int nri = (mr - g + 7) >> 3;
+        for (int kk = 0; kk < kc; ++kk) {
+          TC x = Xs[kk][lane];
+#pragma unroll
+          for (int i = 0; i < RPT; ++i)
+            if (i < nri) cmac(acc[i], As[kk][g + 8 * i], x);
+        }
+        __syncthreads();
+      }
+    }
+    if (col < nrhs) {
+      TV* out = (TV*)vb.p[t.out_buf] + (long long)(t.out_row + r0) * nrhs;
+      const TV* base = (t.mode == 1)
+                           ? (const TV*)vb.p[t.base_buf] + (long long)(t.base_row + r0) * nrhs
+                           : nullptr;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        int r = g + 8 * i;
+        if (r >= mr) continue;
+        TC v = acc[i];
+        if (base) {
+          TC b = cvt<TC, TV>(base[(long long)r * nrhs + col]);
+          v.x += b.x;
+          v.y += b.y;
+        }
+        out[(long long)r * nrhs + col] = cvt<TV, TC>(v);
+      }
+    }
+  }
+}
+
 template <class TV>
 __global__ void k_finalize(const FTask* __restrict__ tasks, const int* __restrict__ slots,
                            VBufs vb, int nrhs) {
@@ -300,8 +380,8 @@ static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int 
   } else if (nrhs <= 8) {
     k_gather_gemm<8, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else {
-    k_gather_gemm<32, TA, TV, TC><<<dim3(nt, (nrhs + 31) / 32), NTHR, 0, s>>>(tl.d_tasks, tl.d_items,
-                                                                              vb, ab, nrhs);
+    k_gather_rows<TA, TV, TC><<<dim3(nt, (nrhs + 31) / 32), 256, 0, s>>>(tl.d_tasks, tl.d_items,
+                                                                         vb, ab, nrhs);
   }
 }
 

@@ -206,3 +206,22 @@ def test_block_file_round_trip(tmp_path):
         assert a[:5] == b[:5] and np.array_equal(a[5], b[5])
     assert d["rows"] == S.rows
     assert all(np.array_equal(d["alpha"][k], S.alpha[k]) for k in S.alpha)
+
+
+def test_c_entries_match_numpy():
+    """oracle/cefie.c states the same EFIE entry as oracle/efie.py."""
+    from oracle.cefie import CBlock
+    v, f = icosphere(2, 0.5)
+    r = build_rwg(v, f)
+    E = EFIE(r)
+    C = CBlock(E)
+    rows = np.arange(0, r.n, 7)
+    cols = np.arange(r.n)
+    a = E.block(rows, cols)
+    b = C(rows, cols)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+    vp, fp = plate(1.0, 8)
+    rp = build_rwg(vp, fp)
+    Ep = EFIE(rp)
+    a = Ep.block(np.arange(rp.n), np.arange(rp.n))
+    assert np.abs(a - CBlock(Ep)(np.arange(rp.n), np.arange(rp.n))).max() < 1e-12 * np.abs(a).max()
