@@ -64,11 +64,18 @@ typedef struct {
   int precision;         /* HM_FP64 or HM_MIXED                                */
   int refine_steps;      /* refinement steps on the FP64 residual (mixed: 1)   */
   long long spin_limit;  /* iteration cap of every device-side wait           */
-  int reserved[8];
+  int tensor_cores;      /* HM_MIXED products on tcgen05 tensor cores (three-way
+                            bf16 split, FP32 accumulation) when nrhs >= 32:
+                            1 (default) or 0 for the CUDA-core FP32 kernels    */
+  int fp64_emulation;    /* HM_MIXED refinement residual (FP64-accurate products)
+                            on tensor cores by exact 7-bit integer slicing of the
+                            FP64 operands: 1 (default), or 0 for the FP64 units  */
+  int reserved[6];
 } hm_params;
 
 /* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,
- * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26. */
+ * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26, tensor_cores 1,
+ * fp64_emulation 1. */
 void hm_default_params(hm_params* p);
 
 /* Build the H-matrix of a closed or open triangulated PEC surface (Sec. II:

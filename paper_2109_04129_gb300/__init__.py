@@ -43,7 +43,8 @@ class hm_params(ctypes.Structure):
                 ("ordering", ctypes.c_int), ("aca_tol", ctypes.c_double),
                 ("fill", ctypes.c_int), ("n_terms", ctypes.c_int),
                 ("precision", ctypes.c_int), ("refine_steps", ctypes.c_int),
-                ("spin_limit", ctypes.c_longlong), ("reserved", ctypes.c_int * 8)]
+                ("spin_limit", ctypes.c_longlong), ("tensor_cores", ctypes.c_int),
+                ("fp64_emulation", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double

@@ -172,6 +172,37 @@ void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
   sw.scratch_rows = max_scr;
 }
 
+// For every task row i: E_i = max over the task's items and inner index of the
+// frexp exponent of |re| and |im| of op(A)(i, k), so that |op(A)(i, k)| < 2^E_i.
+hm_status row_exponents(hm_ctx* h, const TaskList& tl, RowExp& R) {
+  cudaFree(R.d_e);
+  cudaFree(R.d_off);
+  R = RowExp();
+  for (const GTask& t : tl.tasks) {
+    R.off.push_back((long long)R.e.size());
+    std::vector<int> ex(t.m, -1022);
+    for (int q = t.it0; q < t.it1; ++q) {
+      const GItem& it = tl.items[q];
+      const std::vector<cplx>* src = it.a_buf == AB_NEAR ? &h->h_near
+                                     : it.a_buf == AB_FAR ? &h->h_far
+                                     : it.a_buf == AB_ALPHA ? &h->h_alpha : &h->h_dinv;
+      const cplx* A = src->data() + it.a_off;
+      for (int i = 0; i < t.m; ++i)
+        for (int k = 0; k < it.k; ++k) {
+          cplx a = it.trans ? A[(long long)k * it.lda + i] : A[(long long)i * it.lda + k];
+          int e1 = 0, e2 = 0;
+          if (a.x != 0.0) { std::frexp(a.x, &e1); ex[i] = std::max(ex[i], e1); }
+          if (a.y != 0.0) { std::frexp(a.y, &e2); ex[i] = std::max(ex[i], e2); }
+        }
+    }
+    R.e.insert(R.e.end(), ex.begin(), ex.end());
+  }
+  if (R.e.empty()) return HM_OK;
+  hm_status s = upload(&R.d_e, R.e, &h->dev_bytes);
+  if (s) return s;
+  return upload(&R.d_off, R.off, &h->dev_bytes);
+}
+
 hm_status build_schedules(hm_ctx* h) {
   free_sweep(h->fwd);
   free_sweep(h->bwd);
@@ -286,6 +317,9 @@ hm_status build_schedules(hm_ctx* h) {
   hm_status s = upload_tasks(h->far1_tl, b);
   if (!s) s = upload_tasks(h->far2_tl, b);
   if (!s) s = upload_tasks(h->near_tl, b);
+  if (!s) s = row_exponents(h, h->near_tl, h->rexp_near);
+  if (!s) s = row_exponents(h, h->far1_tl, h->rexp_far1);
+  if (!s) s = row_exponents(h, h->far2_tl, h->rexp_far2);
   if (s) return s;
   h->sched_ready = true;
   return HM_OK;
@@ -309,6 +343,8 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
     h->vec_rows[i] = rows[i];
   }
   HM_CUDA(cudaMalloc((void**)&h->d_norms, 4 * sizeof(double) * nrhs));
+  cudaFree(h->d_fexp);
+  HM_CUDA(cudaMalloc((void**)&h->d_fexp, 2 * sizeof(int) * nrhs));
   h->cap_nrhs = nrhs;
   return HM_OK;
 }
@@ -363,13 +399,32 @@ static void tables(hm_ctx* h, void* in, void* out, bool low, VBufs& v, ABufs& a)
   a.p[AB_DINV] = h->d_dinv;
 }
 
+hm_status ensure_err(hm_ctx* h) {
+  if (h->d_err) return HM_OK;
+  HM_CUDA(cudaMalloc((void**)&h->d_err, sizeof(int)));
+  HM_CUDA(cudaMemset(h->d_err, 0, sizeof(int)));
+  return HM_OK;
+}
+
+// complex64 task lists go to the tensor-core kernel for wide RHS batches
+static hm_status launch_any(hm_ctx* h, const TaskList& tl, const VBufs& v, const ABufs& a,
+                            int nrhs, int prec, int* cat) {
+  if (prec == PREC_32 && h->p.tensor_cores && nrhs >= 32 && tc_ok_for(tl)) {
+    hm_status s = ensure_err(h);
+    if (s) return s;
+    if (cat && *cat == PC_MX_SWEEP) *cat = PC_MX_SWEEP;   // same category, tensor path
+    return launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err);
+  }
+  return launch_tasks(tl, v, a, nrhs, h->stream, prec);
+}
+
 hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs, int cat,
                          int prec, bool low) {
   VBufs v;
   ABufs a;
   tables(h, in, out, low, v, a);
   int ev = prof_begin(h);
-  hm_status s = launch_tasks(tl, v, a, nrhs, h->stream, prec);
+  hm_status s = launch_any(h, tl, v, a, nrhs, prec, &cat);
   double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
   prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
   return s;
@@ -383,7 +438,7 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
   double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
   for (size_t l = 0; l < sw.part.size(); ++l) {
     int ev = prof_begin(h);
-    hm_status s = launch_tasks(sw.part[l], v, a, nrhs, h->stream, prec);
+    hm_status s = launch_any(h, sw.part[l], v, a, nrhs, prec, &cat);
     if (s) return s;
     prof_end(h, ev, cat, tl_bytes(sw.part[l], nrhs, asz, vsz), 8.0 * sw.part[l].flops * nrhs);
     ev = prof_begin(h);
@@ -394,6 +449,22 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
     prof_end(h, ev, PC_FIN, fb, 0.0);
   }
   return HM_OK;
+}
+
+// FP64-accurate product of a task list on tensor cores (refinement residual);
+// fexp_in / fexp_far must hold the column exponents of the bound panels.
+hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, int nrhs,
+                      int cat) {
+  hm_status s = ensure_err(h);
+  if (s) return s;
+  VBufs v;
+  ABufs a;
+  tables(h, in, out, false, v, a);
+  int ev = prof_begin(h);
+  s = launch_tasks_oz(tl, v, a, nrhs, h->stream, R.d_e, R.d_off, h->d_fexp,
+                      h->d_fexp + h->cap_nrhs, h->p.spin_limit, h->d_err);
+  prof_end(h, ev, cat, tl_bytes(tl, nrhs), 8.0 * tl.flops * nrhs);
+  return s;
 }
 
 hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
@@ -513,6 +584,8 @@ void hm_default_params(hm_params* p) {
   p->precision = HM_FP64;
   p->refine_steps = 0;
   p->spin_limit = 1LL << 26;
+  p->tensor_cores = 1;
+  p->fp64_emulation = 1;
 }
 
 const char* hm_status_string(hm_status s) {
@@ -838,6 +911,11 @@ hm_status hm_get_diagnostics(hm_handle h, double* ratio, double* resid, int nrhs
   if (nrhs > h->last_nrhs || !h->d_norms) return HM_ERR_STATE;
   std::vector<double> nrm(4 * (size_t)h->cap_nrhs, 0.0);
   HM_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->d_err) {
+    int e = 0;
+    HM_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return HM_ERR_TIMEOUT;
+  }
   HM_CUDA(cudaMemcpy(nrm.data(), h->d_norms, nrm.size() * sizeof(double),
                      cudaMemcpyDeviceToHost));
   bool warn = false;
@@ -914,6 +992,12 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_dinv);
   for (int i = 0; i < NPHYS; ++i) cudaFree(h->d_vec[i]);
   cudaFree(h->d_norms);
+  cudaFree(h->d_err);
+  cudaFree(h->d_fexp);
+  for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2}) {
+    cudaFree(R->d_e);
+    cudaFree(R->d_off);
+  }
   cudaFree(h->d_verts);
   cudaFree(h->d_tris);
   cudaFree(h->d_edge);

@@ -56,6 +56,13 @@ struct TaskList {
   long long flops = 0;    // complex MACs per RHS
   long long a_bytes = 0;  // matrix bytes read per launch
 };
+// per-task row scale exponents of a task list (FP64-accurate tensor products)
+struct RowExp {
+  std::vector<int> e;
+  std::vector<long long> off;
+  int* d_e = nullptr;
+  long long* d_off = nullptr;
+};
 struct FinList {
   std::vector<FTask> tasks;
   std::vector<int> slots;
@@ -132,6 +139,9 @@ struct hm_ctx {
   std::vector<double> verts;
   std::vector<int> tris, edge;
   double* d_norms = nullptr;    // 4 * cap_nrhs
+  int* d_err = nullptr;         // device status word (bounded waits that timed out)
+  hm::RowExp rexp_near, rexp_far1, rexp_far2;
+  int* d_fexp = nullptr;        // 2 * cap_nrhs column exponents
   // profiling (hm_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> evpool;
@@ -155,6 +165,16 @@ hm_status launch_axpby64_32(cplx* o, double sa, const float2* b, double sb, size
 hm_status launch_axpby32(float2* out, const float2* a, float sa, const float2* b, float sb,
                          size_t n, cudaStream_t s);
 hm_status launch_col_norms2_32(const float2* V, int N, int nrhs, double* out, cudaStream_t s);
+// hm_tc.cu: tensor-core gather for complex64 task lists (tasks with 2m <= 256)
+bool tc_ok_for(const TaskList& tl);
+// hm_oz.cu: FP64-accurate products on tensor cores
+hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s);
+hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                          cudaStream_t s, const int* row_exp, const long long* exp_off,
+                          const int* fexp_in, const int* fexp_far, long long spin_limit,
+                          int* err);
+hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
+                          cudaStream_t s, long long spin_limit, int* err);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s);
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,

@@ -188,17 +188,18 @@ __global__ void __launch_bounds__(256) k_gather_rows(const GTask* __restrict__ t
       const TV* X = (const TV*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
       for (int k0 = 0; k0 < I.k; k0 += RK) {
         const int kc = min(RK, I.k - k0);
+        // only the block's mr rows are staged (rows >= mr are never read)
         if (!I.trans) {
-          for (int e = threadIdx.x; e < RR * RK; e += 256) {
+          for (int e = threadIdx.x; e < mr * RK; e += 256) {
             int r = e / RK, kk = e % RK;
-            As[kk][r] = (r < mr && kk < kc) ? cvt<TC, TA>(A[(long long)(r0 + r) * I.lda + k0 + kk])
-                                            : czero<TC>();
+            As[kk][r] = (kk < kc) ? cvt<TC, TA>(A[(long long)(r0 + r) * I.lda + k0 + kk])
+                                  : czero<TC>();
           }
         } else {
-          for (int e = threadIdx.x; e < RR * RK; e += 256) {
-            int kk = e / RR, r = e % RR;
-            As[kk][r] = (r < mr && kk < kc) ? cvt<TC, TA>(A[(long long)(k0 + kk) * I.lda + r0 + r])
-                                            : czero<TC>();
+          for (int e = threadIdx.x; e < mr * RK; e += 256) {
+            int kk = e / mr, r = e % mr;
+            As[kk][r] = (kk < kc) ? cvt<TC, TA>(A[(long long)(k0 + kk) * I.lda + r0 + r])
+                                  : czero<TC>();
           }
         }
         for (int e = threadIdx.x; e < RK * 32; e += 256) {

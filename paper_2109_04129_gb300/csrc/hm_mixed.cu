@@ -7,6 +7,7 @@
 // panels).  Then refine_steps steps of iterative refinement against the FP64
 // residual:  r = b - (Z_N + Z_F) x  (complex128 near blocks and far factors,
 // FP64 products),  x += series(r)  in the same mixed precision.
+#include <algorithm>
 #include <vector>
 
 #include "hm_mixed.h"
@@ -19,6 +20,8 @@ hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs,
 hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, int prec,
                           bool low);
 hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs);
+hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, int nrhs,
+                      int cat);
 }
 
 namespace {
@@ -130,6 +133,31 @@ void* mixed_scratch(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_SCR] 
 void* mixed_fart(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_FAR] : nullptr; }
 }  // namespace hm
 
+// Y (P_Y) = Z_N x and Z (P_Z) = Z_F x for x in P_XT, FP64-accurate products:
+// tensor cores with exact integer slicing, or the FP64 units.
+static hm_status residual_products(hm_ctx* h, int nrhs, bool with_far) {
+  cplx** V = h->d_vec;
+  hm_status s;
+  if (h->p.fp64_emulation && nrhs >= 32) {
+    if ((s = launch_col_exp(V[P_XT], h->N, nrhs, h->d_fexp, h->stream))) return s;
+    if ((s = run_oz_list(h, h->near_tl, h->rexp_near, V[P_XT], V[P_Y], nrhs, PC_NEAR)))
+      return s;
+    if (!with_far) return HM_OK;
+    if ((s = run_oz_list(h, h->far1_tl, h->rexp_far1, V[P_XT], nullptr, nrhs, PC_FAR1)))
+      return s;
+    if ((s = launch_col_exp(h->d_vec[P_FAR], std::max(1, h->far_t_rows), nrhs,
+                            h->d_fexp + h->cap_nrhs, h->stream)))
+      return s;
+    return run_oz_list(h, h->far2_tl, h->rexp_far2, V[P_XT], V[P_Z], nrhs, PC_FAR2);
+  }
+  if ((s = run_chain_list(h, h->near_tl, V[P_XT], V[P_Y], nrhs, PC_NEAR, PREC_64, false)))
+    return s;
+  if (!with_far) return HM_OK;
+  if ((s = run_chain_list(h, h->far1_tl, V[P_XT], nullptr, nrhs, PC_FAR1, PREC_64, false)))
+    return s;
+  return run_chain_list(h, h->far2_tl, V[P_XT], V[P_Z], nrhs, PC_FAR2, PREC_64, false);
+}
+
 hm_status hm_mixed_solve(hm_ctx* h, cplx* X, const cplx* B, int nrhs) {
   Mixed* M = (Mixed*)h->mixed;
   if (!M || !M->alpha) return HM_ERR_STATE;
@@ -145,13 +173,8 @@ hm_status hm_mixed_solve(hm_ctx* h, cplx* X, const cplx* B, int nrhs) {
   HM_CUDA(cudaMemsetAsync(V[P_XT], 0, n * sizeof(cplx), h->stream));
   if ((s = launch_axpby64_32(V[P_XT], 0.0, M->v[Q_XT], 1.0, n, h->stream))) return s;
   for (int step = 0; step < h->p.refine_steps; ++step) {
-    // r = b - (Z_N + Z_F) x  in FP64
-    if ((s = run_chain_list(h, h->near_tl, V[P_XT], V[P_Y], nrhs, PC_NEAR, PREC_64, false)))
-      return s;
-    if ((s = run_chain_list(h, h->far1_tl, V[P_XT], nullptr, nrhs, PC_FAR1, PREC_64, false)))
-      return s;
-    if ((s = run_chain_list(h, h->far2_tl, V[P_XT], V[P_Z], nrhs, PC_FAR2, PREC_64, false)))
-      return s;
+    // r = b - (Z_N + Z_F) x  with FP64-accurate products
+    if ((s = residual_products(h, nrhs, true))) return s;
     if ((s = launch_axpby(V[P_Y], V[P_Y], -1.0, V[P_Z], -1.0, n, h->stream))) return s;
     if ((s = launch_axpby(V[P_R], V[P_B], 1.0, V[P_Y], 1.0, n, h->stream))) return s;
     if (step == h->p.refine_steps - 1) {
@@ -175,6 +198,17 @@ hm_status hm_mixed_apply(hm_ctx* h, int op, cplx* Y, const cplx* X, int nrhs) {
   if (s) return s;
   cplx** V = h->d_vec;
   const size_t n = (size_t)h->N * nrhs;
+  if (op == HM_OP_NEAR || op == HM_OP_Z) {
+    // the refinement's FP64-accurate products
+    if ((s = launch_gather_perm(X, V[P_XT], h->d_perm, h->N, nrhs, h->stream))) return s;
+    if ((s = residual_products(h, nrhs, op == HM_OP_Z))) return s;
+    if (op == HM_OP_Z &&
+        (s = launch_axpby(V[P_Y], V[P_Y], 1.0, V[P_Z], 1.0, n, h->stream)))
+      return s;
+    if ((s = launch_scatter_perm(V[P_Y], Y, h->d_perm, h->N, nrhs, h->stream))) return s;
+    HM_CUDA(cudaStreamSynchronize(h->stream));
+    return HM_OK;
+  }
   if ((s = launch_gather_perm(X, V[P_B], h->d_perm, h->N, nrhs, h->stream))) return s;
   if ((s = launch_to32(V[P_B], M->v[Q_B], n, h->stream))) return s;
   float2* res = M->v[Q_Y];

@@ -163,3 +163,47 @@ def test_mixed_operator_parity(op):
         sol.apply(op, Y, to_dev(X))
         err = rel(from_dev(Y), _oracle_op(H, S, op, X))
         assert err.max() < 2e-5, (op, nrhs, err.max())
+
+
+@pytest.mark.parametrize("name", ["sphere_r0.25_L2", "plate_2l"])
+def test_mixed_tensor_core_solve(name):
+    """nrhs >= 32 runs the mixed products on tcgen05 (three-way bf16 split,
+    FP32 accumulation): same 1e-4 bar against the oracle's FP64 series plus
+    refinement, and close to the CUDA-core FP32 path."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from oracle.series import refine_once
+    w, H, S, B = case(name)
+    Bw = np.concatenate([B, rand_panel(H.N, 40, 77) * np.abs(B).max()], axis=1)   # 52+ RHS
+    x2, _ = series_solve(H, S, Bw, 2)
+    want = refine_once(H, S, Bw, x2)
+    out = {}
+    for tc in (1, 0):
+        sol = load_case(H, S, precision=hp.HM_MIXED, refine_steps=1, tensor_cores=tc)
+        X = torch.empty((Bw.shape[1], H.N), dtype=torch.complex128, device="cuda")
+        sol.solve(X, to_dev(Bw))
+        assert hp._lib.hm_get_diagnostics(sol._h, None, None, Bw.shape[1]) in (0, 100)
+        out[tc] = from_dev(X)
+        err = rel(out[tc], want)
+        assert err.max() <= 1e-4, (name, tc, err.max())
+    assert rel(out[1], out[0]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["sphere_r0.25_L2", "plate_2l", "sphere_r0.5_L3"])
+@pytest.mark.parametrize("op", ["NEAR", "Z"])
+def test_fp64_emulated_products(name, op):
+    """Refinement-residual products of a mixed handle (nrhs >= 32: bf16 tensor
+    cores with exact 7-bit integer slicing of the FP64 operands) against the
+    oracle's FP64 products: relative error <= 1e-12 per RHS."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    w, H, S, B = case(name)
+    sol = load_case(H, S, precision=hp.HM_MIXED, refine_steps=1)
+    for nrhs, seed in ((33, 5), (130, 6)):
+        X = rand_panel(H.N, nrhs, seed)
+        X[:, 0] *= 1e-6            # a column far below the others' scale
+        Y = torch.empty((nrhs, H.N), dtype=torch.complex128, device="cuda")
+        sol.apply(op, Y, to_dev(X))
+        err = rel(from_dev(Y), _oracle_op(H, S, op, X))
+        assert err.max() < 1e-12, (name, op, nrhs, err.max())
+    assert hp._lib.hm_get_diagnostics(sol._h, None, None, 1) != hp.HM_ERR_TIMEOUT
