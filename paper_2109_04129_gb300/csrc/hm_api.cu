@@ -320,6 +320,7 @@ hm_status build_schedules(hm_ctx* h) {
   if (!s) s = row_exponents(h, h->near_tl, h->rexp_near);
   if (!s) s = row_exponents(h, h->far1_tl, h->rexp_far1);
   if (!s) s = row_exponents(h, h->far2_tl, h->rexp_far2);
+  if (!s && h->has_scaling) s = row_exponents(h, h->dinv_tl, h->rexp_dinv);
   if (s) return s;
   h->sched_ready = true;
   return HM_OK;
@@ -454,7 +455,7 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
 // FP64-accurate product of a task list on tensor cores (refinement residual);
 // fexp_in / fexp_far must hold the column exponents of the bound panels.
 hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, int nrhs,
-                      int cat) {
+                      int cat, bool panels32) {
   hm_status s = ensure_err(h);
   if (s) return s;
   VBufs v;
@@ -462,8 +463,8 @@ hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, i
   tables(h, in, out, false, v, a);
   int ev = prof_begin(h);
   s = launch_tasks_oz(tl, v, a, nrhs, h->stream, R.d_e, R.d_off, h->d_fexp,
-                      h->d_fexp + h->cap_nrhs, h->p.spin_limit, h->d_err);
-  prof_end(h, ev, cat, tl_bytes(tl, nrhs), 8.0 * tl.flops * nrhs);
+                      h->d_fexp + h->cap_nrhs, h->p.spin_limit, h->d_err, panels32);
+  prof_end(h, ev, cat, tl_bytes(tl, nrhs, 16, panels32 ? 8 : 16), 8.0 * tl.flops * nrhs);
   return s;
 }
 
@@ -872,6 +873,29 @@ hm_status hm_power_series_solve(hm_handle h, void* X, const void* B, int nrhs) {
       if ((s = launch_gather_perm((const cplx*)B, V[P_B], h->d_perm, h->N, nrhs, h->stream)))
         return s;
       if ((s = series_fp64(h, nrhs, true))) return s;
+      // optional refinement in FP64: r = b - (Z_N + Z_F) x, x += series(r)
+      for (int step = 0; step < h->p.refine_steps; ++step) {
+        const size_t n = (size_t)h->N * nrhs;
+        // keep x (P_X0) and b (P_B0); the residual goes to P_B for the series
+        HM_CUDA(cudaMemcpyAsync(V[P_X0], V[P_XT], n * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                                h->stream));
+        HM_CUDA(cudaMemcpyAsync(V[P_B0], V[P_B], n * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                                h->stream));
+        if ((s = run_list(h, h->near_tl, V[P_X0], V[P_Y], nrhs, PC_NEAR))) return s;
+        if ((s = apply_far(h, V[P_X0], V[P_Z], nrhs))) return s;
+        if ((s = launch_axpby(V[P_Y], V[P_Y], -1.0, V[P_Z], -1.0, n, h->stream))) return s;
+        if ((s = launch_axpby(V[P_B], V[P_B0], 1.0, V[P_Y], 1.0, n, h->stream))) return s;
+        if (step == h->p.refine_steps - 1) {
+          if ((s = launch_col_norms2(V[P_B0], h->N, nrhs, h->d_norms + 2 * nrhs, h->stream)))
+            return s;
+          if ((s = launch_col_norms2(V[P_B], h->N, nrhs, h->d_norms + 3 * nrhs, h->stream)))
+            return s;
+        }
+        if ((s = series_fp64(h, nrhs, false))) return s;       // P_XT = series(r)
+        if ((s = launch_axpby(V[P_XT], V[P_XT], 1.0, V[P_X0], 1.0, n, h->stream))) return s;
+        HM_CUDA(cudaMemcpyAsync(V[P_B], V[P_B0], n * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                                h->stream));
+      }
       s = launch_scatter_perm(V[P_XT], (cplx*)X, h->d_perm, h->N, nrhs, h->stream);
       h->ratio.assign(nrhs, 0.0);
       h->resid.assign(nrhs, 0.0);
@@ -926,8 +950,7 @@ hm_status hm_get_diagnostics(hm_handle h, double* ratio, double* resid, int nrhs
     if (q > 0.1 && h->p.n_terms >= 2) warn = true;
     if (resid) {
       double bb = nrm[2 * h->last_nrhs + r], rr = nrm[3 * h->last_nrhs + r];
-      resid[r] = (h->p.precision == HM_MIXED && h->p.refine_steps > 0 && bb > 0)
-                     ? std::sqrt(rr / bb) : 0.0;
+      resid[r] = (h->p.refine_steps > 0 && bb > 0) ? std::sqrt(rr / bb) : 0.0;
     }
   }
   return warn ? HM_WARN_SERIES_RATIO : HM_OK;
@@ -994,7 +1017,7 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_norms);
   cudaFree(h->d_err);
   cudaFree(h->d_fexp);
-  for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2}) {
+  for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2, &h->rexp_dinv}) {
     cudaFree(R->d_e);
     cudaFree(R->d_off);
   }

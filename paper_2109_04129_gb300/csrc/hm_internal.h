@@ -43,7 +43,8 @@ enum { P_B = 0, P_BO = 1, P_Y = 2, P_Z = 3, P_IT = 4, P_XT = 5, P_R = 6,
        P_SCR = 7,   // split-K scratch (sweep scratch rows)
        P_FAR = 8,   // far-field stage-1 panels (2 * sum of ranks rows)
        P_HB = 9, P_HX = 10,   // staging of host-buffer solves
-       NPHYS = 11 };
+       P_X0 = 11, P_B0 = 12,  // FP64 refinement: saved x and b
+       NPHYS = 13 };
 // matrix buffers
 enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3 };
 
@@ -140,7 +141,7 @@ struct hm_ctx {
   std::vector<int> tris, edge;
   double* d_norms = nullptr;    // 4 * cap_nrhs
   int* d_err = nullptr;         // device status word (bounded waits that timed out)
-  hm::RowExp rexp_near, rexp_far1, rexp_far2;
+  hm::RowExp rexp_near, rexp_far1, rexp_far2, rexp_dinv;
   int* d_fexp = nullptr;        // 2 * cap_nrhs column exponents
   // profiling (hm_profile_enable)
   bool prof = false;
@@ -169,10 +170,11 @@ hm_status launch_col_norms2_32(const float2* V, int N, int nrhs, double* out, cu
 bool tc_ok_for(const TaskList& tl);
 // hm_oz.cu: FP64-accurate products on tensor cores
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s);
+hm_status launch_col_exp32(const float2* V, int rows, int nrhs, int* out, cudaStream_t s);
 hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, const int* row_exp, const long long* exp_off,
                           const int* fexp_in, const int* fexp_far, long long spin_limit,
-                          int* err);
+                          int* err, bool panels32 = false);
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, long long spin_limit, int* err);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,

@@ -401,7 +401,14 @@ hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int
 
 hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s, int prec) {
   if (fl.tasks.empty()) return HM_OK;
-  int ny = nrhs >= 64 ? 8 : 1;
+  // about one element per thread: the slot reads of different elements are
+  // independent, so a wide grid hides their latency on narrow levels
+  int mmax = 1;
+  for (const FTask& f : fl.tasks) mmax = f.m > mmax ? f.m : mmax;
+  long long per_task = (long long)mmax * nrhs;
+  int ny = (int)((per_task + 255) / 256);
+  if (ny > 512) ny = 512;
+  if (ny < 1) ny = 1;
   if (prec == PREC_64)
     k_finalize<double2><<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots,
                                                                             vb, nrhs);

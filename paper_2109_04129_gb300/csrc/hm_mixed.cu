@@ -21,7 +21,7 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
                           bool low);
 hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs);
 hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, int nrhs,
-                      int cat);
+                      int cat, bool panels32 = false);
 }
 
 namespace {
@@ -71,14 +71,24 @@ hm_status copy32(hm_ctx* h, float2* d, const float2* s, int nrhs) {
   return HM_OK;
 }
 
+// D^-1 (complex128) applied to a complex64 panel: FP64-accurate products on the
+// tensor cores (exact integer slicing) for wide batches, else the FP64 units
+hm_status dinv32(hm_ctx* h, float2* in, float2* out, int nrhs) {
+  if (h->p.fp64_emulation && nrhs >= 32) {
+    hm_status s = launch_col_exp32(in, h->N, nrhs, h->d_fexp, h->stream);
+    if (s) return s;
+    return run_oz_list(h, h->dinv_tl, h->rexp_dinv, in, out, nrhs, PC_DINV, true);
+  }
+  return run_chain_list(h, h->dinv_tl, in, out, nrhs, PC_DINV, PREC_64x32, true);
+}
+
 // x32 (Q_XT) = series(b32 in Q_B); ratio norms when diag
 hm_status series32(hm_ctx* h, Mixed* M, int nrhs, bool diag) {
   float2** V = M->v;
   hm_status s;
   if ((s = copy32(h, V[Q_Y], V[Q_B], nrhs))) return s;
   if ((s = run_chain_sweep(h, h->fwd, V[Q_Y], nrhs, PC_MX_SWEEP, PREC_32, true))) return s;
-  if ((s = run_chain_list(h, h->dinv_tl, V[Q_Y], V[Q_BO], nrhs, PC_DINV, PREC_64x32, true)))
-    return s;
+  if ((s = dinv32(h, V[Q_Y], V[Q_BO], nrhs))) return s;
   if ((s = copy32(h, V[Q_XT], V[Q_BO], nrhs))) return s;
   float2* it = V[Q_BO];
   for (int t = 1; t < h->p.n_terms; ++t) {
@@ -87,8 +97,7 @@ hm_status series32(hm_ctx* h, Mixed* M, int nrhs, bool diag) {
     if ((s = mixed_far(h, V[Q_Y], V[Q_Z], nrhs))) return s;
     if ((s = run_chain_sweep(h, h->fwd, V[Q_Z], nrhs, PC_MX_SWEEP, PREC_32, true))) return s;
     float2* nxt = (it == V[Q_IT]) ? V[Q_R] : V[Q_IT];
-    if ((s = run_chain_list(h, h->dinv_tl, V[Q_Z], nxt, nrhs, PC_DINV, PREC_64x32, true)))
-      return s;
+    if ((s = dinv32(h, V[Q_Z], nxt, nrhs))) return s;
     if (t == 1 && diag) {
       if ((s = launch_col_norms2_32(it, h->N, nrhs, h->d_norms, h->stream))) return s;
       if ((s = launch_col_norms2_32(nxt, h->N, nrhs, h->d_norms + nrhs, h->stream))) return s;
@@ -222,7 +231,7 @@ hm_status hm_mixed_apply(hm_ctx* h, int op, cplx* Y, const cplx* X, int nrhs) {
       s = run_chain_sweep(h, h->bwd, M->v[Q_Y], nrhs, PC_MX_SWEEP, PREC_32, true);
       break;
     case HM_OP_DINV:
-      s = run_chain_list(h, h->dinv_tl, M->v[Q_B], M->v[Q_Y], nrhs, PC_DINV, PREC_64x32, true);
+      s = dinv32(h, M->v[Q_B], M->v[Q_Y], nrhs);
       break;
     case HM_OP_FAR:
       s = mixed_far(h, M->v[Q_B], M->v[Q_Y], nrhs);

@@ -94,6 +94,16 @@ __device__ __forceinline__ void digits(double v, int S, __nv_bfloat16* d) {
   }
 }
 
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ void put(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void put(float2* p, double2 v) {
+  *p = make_float2((float)v.x, (float)v.y);
+}
+
+// TX / TY: element type of the input / output panels (complex128 or complex64;
+// complex64 inputs are widened exactly before slicing)
+template <class TX, class TY>
 __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
     const GTask* __restrict__ tasks, const GItem* __restrict__ items, VBufs vb, ABufs ab,
     int nrhs, const int* __restrict__ task_row_exp, const long long* __restrict__ task_exp_off,
@@ -187,13 +197,13 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
       F = (col < nrhs) ? fe[col] : 0;
     }
     const double2* A = (const double2*)ab.p[I.a_buf] + I.a_off;
-    const double2* X = (const double2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+    const TX* X = (const TX*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
     for (int k0 = 0; k0 < I.k && ok; k0 += OZ_KC) {
       const int kc = min(OZ_KC, I.k - k0);
       if (pending && win + kc > OZ_WIN) flush();
       // ---- X' digits: thread = RHS row
       for (int kk = 0; kk < OZ_KC; ++kk) {
-        double2 x = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
+        double2 x = (kk < kc && col < nrhs) ? to_d2(X[(long long)(k0 + kk) * nrhs + col])
                                             : make_double2(0.0, 0.0);
         __nv_bfloat16 dr[OZ_NS], di[OZ_NS];
         digits(x.x, F, dr);
@@ -267,18 +277,17 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   }
   if (ok && pending) flush();
   if (ok && col < nrhs) {
-    double2* out = (double2*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
-    const double2* base = (t.mode == 1)
-                              ? (const double2*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
-                              : nullptr;
+    TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
+    const TY* base = (t.mode == 1) ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
+                                   : nullptr;
     for (int i = 0; i < nr; ++i) {
       double2 y = make_double2(acc[2 * i], acc[2 * i + 1]);
       if (base) {
-        double2 b = base[(long long)i * nrhs + col];
+        double2 b = to_d2(base[(long long)i * nrhs + col]);
         y.x += b.x;
         y.y += b.y;
       }
-      out[(long long)i * nrhs + col] = y;
+      put(out + (long long)i * nrhs + col, y);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -287,16 +296,24 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
+__device__ __forceinline__ unsigned int bexp(double v) {
+  return (unsigned int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+// biased FP64 exponent of a float's value (0 for zero / subnormal floats)
+__device__ __forceinline__ unsigned int bexp(float v) {
+  unsigned int e = (__float_as_uint(v) >> 23) & 0xFF;
+  return e == 0 ? 0u : e - 127u + 1023u;
+}
+
 // F_r = smallest S with max_k max(|re|, |im|) of panel column r < 2^S
-__global__ void k_col_exp(const double2* __restrict__ V, int rows, int nrhs, int* out) {
+template <class TV>
+__global__ void k_col_exp(const TV* __restrict__ V, int rows, int nrhs, int* out) {
   __shared__ unsigned int red[256];
   const int r = blockIdx.x;
   unsigned int m = 0;      // max biased exponent seen
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    double2 v = V[(long long)i * nrhs + r];
-    unsigned int ex = (unsigned int)((__double_as_longlong(v.x) >> 52) & 0x7FF);
-    unsigned int ey = (unsigned int)((__double_as_longlong(v.y) >> 52) & 0x7FF);
-    m = max(m, max(ex, ey));
+    TV v = V[(long long)i * nrhs + r];
+    m = max(m, max(bexp(v.x), bexp(v.y)));
   }
   red[threadIdx.x] = m;
   __syncthreads();
@@ -319,7 +336,13 @@ int oz_max_passes(const TaskList& tl) {
 }
 
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s) {
-  k_col_exp<<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
+  k_col_exp<double2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
+  HM_CUDA(cudaGetLastError());
+  return HM_OK;
+}
+
+hm_status launch_col_exp32(const float2* V, int rows, int nrhs, int* out, cudaStream_t s) {
+  k_col_exp<float2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
@@ -327,18 +350,24 @@ hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream
 hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, const int* row_exp, const long long* exp_off,
                           const int* fexp_in, const int* fexp_far, long long spin_limit,
-                          int* err) {
+                          int* err, bool panels32) {
   if (tl.tasks.empty()) return HM_OK;
   static bool attr = false;
   if (!attr) {
-    HM_CUDA(cudaFuncSetAttribute(k_oz_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 OZ_SMEM));
+    HM_CUDA(cudaFuncSetAttribute(k_oz_gather<double2, double2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    HM_CUDA(cudaFuncSetAttribute(k_oz_gather<float2, float2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     attr = true;
   }
   dim3 grid((unsigned)tl.tasks.size(), (unsigned)((nrhs + OZ_M - 1) / OZ_M),
             (unsigned)oz_max_passes(tl));
-  k_oz_gather<<<grid, OZ_THREADS, OZ_SMEM, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs, row_exp,
-                                                exp_off, fexp_in, fexp_far, spin_limit, err);
+  if (panels32)
+    k_oz_gather<float2, float2><<<grid, OZ_THREADS, OZ_SMEM, s>>>(
+        tl.d_tasks, tl.d_items, vb, ab, nrhs, row_exp, exp_off, fexp_in, fexp_far, spin_limit, err);
+  else
+    k_oz_gather<double2, double2><<<grid, OZ_THREADS, OZ_SMEM, s>>>(
+        tl.d_tasks, tl.d_items, vb, ab, nrhs, row_exp, exp_off, fexp_in, fexp_far, spin_limit, err);
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }

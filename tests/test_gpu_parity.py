@@ -207,3 +207,20 @@ def test_fp64_emulated_products(name, op):
         err = rel(from_dev(Y), _oracle_op(H, S, op, X))
         assert err.max() < 1e-12, (name, op, nrhs, err.max())
     assert hp._lib.hm_get_diagnostics(sol._h, None, None, 1) != hp.HM_ERR_TIMEOUT
+
+
+def test_fp64_refinement_parity():
+    """FP64 chain with one refinement step vs the oracle's FP64 series plus
+    the same refinement (the like-for-like comparator of the mixed chain)."""
+    import torch
+    from oracle.series import refine_once
+    for name in ("sphere_r0.25_L2", "plate_2l"):
+        w, H, S, B = case(name)
+        sol = load_case(H, S, refine_steps=1)
+        X = torch.empty((B.shape[1], H.N), dtype=torch.complex128, device="cuda")
+        sol.solve(X, to_dev(B))
+        x2, _ = series_solve(H, S, B, 2)
+        want = refine_once(H, S, B, x2)
+        assert rel(from_dev(X), want).max() <= 1e-6
+        r, resid = sol.diagnostics(B.shape[1])
+        assert np.all(resid > 0)
