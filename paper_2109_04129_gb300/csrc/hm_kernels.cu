@@ -188,25 +188,45 @@ __global__ void __launch_bounds__(256) k_gather_rows(const GTask* __restrict__ t
       const TV* X = (const TV*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
       for (int k0 = 0; k0 < I.k; k0 += RK) {
         const int kc = min(RK, I.k - k0);
-        // only the block's mr rows are staged (rows >= mr are never read)
-        if (!I.trans) {
-          for (int e = threadIdx.x; e < mr * RK; e += 256) {
-            int r = e / RK, kk = e % RK;
-            As[kk][r] = (kk < kc) ? cvt<TC, TA>(A[(long long)(r0 + r) * I.lda + k0 + kk])
-                                  : czero<TC>();
+        // only the block's mr rows are staged (rows >= mr are never read); every
+        // thread issues all of its loads before storing (one memory latency)
+        {
+          constexpr int EA = RR * RK / 256;     // 8
+          TC av[EA];
+#pragma unroll
+          for (int q = 0; q < EA; ++q) {
+            const int e = threadIdx.x + q * 256;
+            int r, kk;
+            if (!I.trans) { r = e / RK; kk = e % RK; } else { kk = e / mr; r = e % mr; }
+            av[q] = (e < mr * RK && kk < kc)
+                        ? cvt<TC, TA>(I.trans ? A[(long long)(k0 + kk) * I.lda + r0 + r]
+                                              : A[(long long)(r0 + r) * I.lda + k0 + kk])
+                        : czero<TC>();
           }
-        } else {
-          for (int e = threadIdx.x; e < mr * RK; e += 256) {
-            int kk = e / mr, r = e % mr;
-            As[kk][r] = (kk < kc) ? cvt<TC, TA>(A[(long long)(k0 + kk) * I.lda + r0 + r])
-                                  : czero<TC>();
+          constexpr int EX = RK * 32 / 256;     // 2
+          TC xv[EX];
+#pragma unroll
+          for (int q = 0; q < EX; ++q) {
+            const int e = threadIdx.x + q * 256;
+            const int kk = e >> 5, c = e & 31;
+            const int cc = blockIdx.y * 32 + c;
+            xv[q] = (kk < kc && cc < nrhs) ? cvt<TC, TV>(X[(long long)(k0 + kk) * nrhs + cc])
+                                           : czero<TC>();
           }
-        }
-        for (int e = threadIdx.x; e < RK * 32; e += 256) {
-          int kk = e >> 5, c = e & 31;
-          int cc = blockIdx.y * 32 + c;
-          Xs[kk][c] = (kk < kc && cc < nrhs) ? cvt<TC, TV>(X[(long long)(k0 + kk) * nrhs + cc])
-                                             : czero<TC>();
+#pragma unroll
+          for (int q = 0; q < EA; ++q) {
+            const int e = threadIdx.x + q * 256;
+            if (e < mr * RK) {
+              int r, kk;
+              if (!I.trans) { r = e / RK; kk = e % RK; } else { kk = e / mr; r = e % mr; }
+              As[kk][r] = av[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < EX; ++q) {
+            const int e = threadIdx.x + q * 256;
+            Xs[e >> 5][e & 31] = xv[q];
+          }
         }
         __syncthreads();
         // rows g, g+8, ... below mr only (warp-uniform bound: no divergence)

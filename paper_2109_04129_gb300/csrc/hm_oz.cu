@@ -41,7 +41,7 @@ constexpr int OZ_LV = 8;                  // levels kept (p + q <= 7)
 constexpr int OZ_RC = 32;                 // complex output rows per CTA
 constexpr int OZ_N = 64;                  // MMA N (2 * OZ_RC)
 constexpr int OZ_WIN = 512;               // complex inner rows per exact window
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;          // two halves share the digit staging
 constexpr int OZ_A_BYTES = OZ_M * OZ_KR * 2;      // one digit plane of X' (8 KB)
 constexpr int OZ_B_BYTES = OZ_N * OZ_KR * 2;      // one digit plane of B' (4 KB)
 constexpr int OZ_SMEM = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES) + 1024;
@@ -121,7 +121,12 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   if (rp >= t.m) return;                                  // whole CTA: uniform
   const int nr = min(OZ_RC, t.m - rp);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int col = blockIdx.y * OZ_M + tid;                // this thread's RHS
+  const int row = tid & (OZ_M - 1);                       // RHS row (TMEM lane) of this thread
+  const int half = tid >> 7;                              // staging half (inner rows)
+  const bool owner = half == 0;                           // warps 0-3 read TMEM, own acc
+  const int col = blockIdx.y * OZ_M + row;                // this thread's RHS
+  // MMA N: the rows of this CTA, rounded up to 16 (at least 32)
+  const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
   const uint32_t bar = smem_u32(&mbar);
   if (tid < OZ_RC) rexp[tid] = (tid < nr) ? task_row_exp[task_exp_off[blockIdx.x] + rp + tid] : 0;
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_N >> 3) << 17) |
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_real >> 3) << 17) |
                          ((uint32_t)(OZ_M >> 4) << 24);
   double acc[OZ_N];
 #pragma unroll
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   auto flush = [&]() {
     // all MMAs of the window completed (each stage waited on its commit)
     asm volatile("tcgen05.fence::after_thread_sync;");
-    for (int c0 = 0; c0 < OZ_N; c0 += 16) {
+    for (int c0 = 0; owner && c0 < n_real; c0 += 16) {
       long long hi[16], lo[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -201,43 +206,72 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
     for (int k0 = 0; k0 < I.k && ok; k0 += OZ_KC) {
       const int kc = min(OZ_KC, I.k - k0);
       if (pending && win + kc > OZ_WIN) flush();
-      // ---- X' digits: thread = RHS row
-      for (int kk = 0; kk < OZ_KC; ++kk) {
-        double2 x = (kk < kc && col < nrhs) ? to_d2(X[(long long)(k0 + kk) * nrhs + col])
-                                            : make_double2(0.0, 0.0);
-        __nv_bfloat16 dr[OZ_NS], di[OZ_NS];
-        digits(x.x, F, dr);
-        digits(x.y, F, di);
+      // ---- X' digits: thread = RHS row, the two halves split the inner rows;
+      // all loads of the thread are issued before any use (one memory latency)
+      {
+        constexpr int KH = OZ_KC / 2;
+        double2 xv[KH];
 #pragma unroll
-        for (int s = 0; s < OZ_NS; ++s) {
-          *(__nv_bfloat16*)(sA + s * OZ_A_BYTES + kmaj(tid, 2 * kk)) = dr[s];
-          *(__nv_bfloat16*)(sA + s * OZ_A_BYTES + kmaj(tid, 2 * kk + 1)) = di[s];
+        for (int j = 0; j < KH; ++j) {
+          const int kk = half * KH + j;
+          xv[j] = (kk < kc && col < nrhs) ? to_d2(X[(long long)(k0 + kk) * nrhs + col])
+                                          : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int kk = half * KH + j;
+          __nv_bfloat16 dr[OZ_NS], di[OZ_NS];
+          digits(xv[j].x, F, dr);
+          digits(xv[j].y, F, di);
+#pragma unroll
+          for (int s = 0; s < OZ_NS; ++s) {
+            *(__nv_bfloat16*)(sA + s * OZ_A_BYTES + kmaj(row, 2 * kk)) = dr[s];
+            *(__nv_bfloat16*)(sA + s * OZ_A_BYTES + kmaj(row, 2 * kk + 1)) = di[s];
+          }
         }
       }
-      // ---- B' digits: element (i, kk) of op(A), rows rp + i
-      for (int e = tid; e < OZ_RC * OZ_KC; e += OZ_THREADS) {
-        int i, kk;
-        if (I.trans) {
-          kk = e / OZ_RC;
-          i = e % OZ_RC;
-        } else {
-          i = e / OZ_KC;
-          kk = e % OZ_KC;
-        }
-        double2 a = make_double2(0.0, 0.0);
-        if (i < nr && kk < kc)
-          a = I.trans ? A[(long long)(k0 + kk) * I.lda + rp + i]
-                      : A[(long long)(rp + i) * I.lda + k0 + kk];
-        __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
-        digits(a.x, rexp[i], ar);
-        digits(a.y, rexp[i], ai);
+      // ---- B' digits: element (i, kk) of op(A), rows rp + i; loads first
+      {
+        constexpr int EMAX = OZ_RC * OZ_KC / OZ_THREADS;     // 2
+        double2 av[EMAX];
 #pragma unroll
-        for (int s = 0; s < OZ_NS; ++s) {
-          unsigned char* bp = sB + s * OZ_B_BYTES;
-          *(__nv_bfloat16*)(bp + kmaj(2 * i, 2 * kk)) = ar[s];
-          *(__nv_bfloat16*)(bp + kmaj(2 * i, 2 * kk + 1)) = __hneg(ai[s]);
-          *(__nv_bfloat16*)(bp + kmaj(2 * i + 1, 2 * kk)) = ai[s];
-          *(__nv_bfloat16*)(bp + kmaj(2 * i + 1, 2 * kk + 1)) = ar[s];
+        for (int q = 0; q < EMAX; ++q) {
+          const int e = tid + q * OZ_THREADS;
+          int i, kk;
+          if (I.trans) {
+            kk = e / OZ_RC;
+            i = e % OZ_RC;
+          } else {
+            i = e / OZ_KC;
+            kk = e % OZ_KC;
+          }
+          av[q] = make_double2(0.0, 0.0);
+          if (i < nr && kk < kc)
+            av[q] = I.trans ? A[(long long)(k0 + kk) * I.lda + rp + i]
+                            : A[(long long)(rp + i) * I.lda + k0 + kk];
+        }
+#pragma unroll
+        for (int q = 0; q < EMAX; ++q) {
+          const int e = tid + q * OZ_THREADS;
+          int i, kk;
+          if (I.trans) {
+            kk = e / OZ_RC;
+            i = e % OZ_RC;
+          } else {
+            i = e / OZ_KC;
+            kk = e % OZ_KC;
+          }
+          __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
+          digits(av[q].x, rexp[i], ar);
+          digits(av[q].y, rexp[i], ai);
+#pragma unroll
+          for (int s = 0; s < OZ_NS; ++s) {
+            unsigned char* bp = sB + s * OZ_B_BYTES;
+            *(__nv_bfloat16*)(bp + kmaj(2 * i, 2 * kk)) = ar[s];
+            *(__nv_bfloat16*)(bp + kmaj(2 * i, 2 * kk + 1)) = __hneg(ai[s]);
+            *(__nv_bfloat16*)(bp + kmaj(2 * i + 1, 2 * kk)) = ai[s];
+            *(__nv_bfloat16*)(bp + kmaj(2 * i + 1, 2 * kk + 1)) = ar[s];
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;");
@@ -276,7 +310,7 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
     }
   }
   if (ok && pending) flush();
-  if (ok && col < nrhs) {
+  if (ok && owner && col < nrhs) {
     TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
     const TY* base = (t.mode == 1) ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
                                    : nullptr;

@@ -32,7 +32,7 @@ constexpr int TC_KC = 16;        // complex inner rows per stage (K = 32 real)
 constexpr int TC_KR = 2 * TC_KC;
 constexpr int TC_NS = 3;         // bf16 slices per operand
 constexpr int TC_NMAX = 256;     // max MMA N (2 * 128 complex rows)
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;     // two halves share the staging; warps 0-3 own TMEM rows
 constexpr int A_SLICE_BYTES = TC_M * TC_KR * 2;       // 8 KB
 constexpr int B_SLICE_BYTES = TC_NMAX * TC_KR * 2;    // 16 KB
 constexpr int TC_SMEM = TC_NS * (A_SLICE_BYTES + B_SLICE_BYTES) + 1024;
@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gather(const GTask* __restric
   __shared__ uint32_t tmem_base;
   const GTask t = tasks[blockIdx.x];
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (TC_M - 1), half = tid >> 7;
   const int r0 = blockIdx.y * TC_M;
   const int n_real = ((2 * t.m + 15) / 16) * 16;             // MMA N
   const uint32_t ncols = n_real <= 32 ? 32 : (n_real <= 64 ? 64 : (n_real <= 128 ? 128 : 256));
@@ -114,45 +115,76 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gather(const GTask* __restric
     const float2* X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
     for (int k0 = 0; k0 < I.k && ok; k0 += TC_KC) {
       const int kc = min(TC_KC, I.k - k0);
-      // ---- stage X' (128 RHS x 32): thread = RHS row
+      // ---- stage X' (128 RHS x 32): thread = RHS row, halves split the inner rows;
+      // all loads of the thread are issued before any use (one memory latency)
       {
-        const int r = tid;
+        const int r = row;
         const int col = r0 + r;
-        for (int kk = 0; kk < TC_KC; ++kk) {
-          float2 x = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
-                                             : make_float2(0.f, 0.f);
+        constexpr int KH = TC_KC / 2;
+        float2 xv[KH];
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int kk = half * KH + j;
+          xv[j] = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
+                                          : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int kk = half * KH + j;
           __nv_bfloat16 sr[TC_NS], si[TC_NS];
-          split3(x.x, sr);
-          split3(x.y, si);
+          split3(xv[j].x, sr);
+          split3(xv[j].y, si);
+#pragma unroll
           for (int s = 0; s < TC_NS; ++s) {
             *(__nv_bfloat16*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = sr[s];
             *(__nv_bfloat16*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk + 1)) = si[s];
           }
         }
       }
-      // ---- stage B' (n_real rows x 32): element (i, kk) of op(A)
-      for (int e = tid; e < (n_real / 2) * TC_KC; e += TC_THREADS) {
-        int i, kk;
-        if (I.trans) {
-          kk = e / (n_real / 2);
-          i = e % (n_real / 2);
-        } else {
-          i = e / TC_KC;
-          kk = e % TC_KC;
+      // ---- stage B' (n_real rows x 32): element (i, kk) of op(A); loads first
+      {
+        constexpr int EMAX = (TC_NMAX / 2) * TC_KC / TC_THREADS;   // 8
+        const int ne = (n_real / 2) * TC_KC;
+        float2 av[EMAX];
+#pragma unroll
+        for (int q = 0; q < EMAX; ++q) {
+          const int e = tid + q * TC_THREADS;
+          int i, kk;
+          if (I.trans) {
+            kk = e / (n_real / 2);
+            i = e % (n_real / 2);
+          } else {
+            i = e / TC_KC;
+            kk = e % TC_KC;
+          }
+          av[q] = make_float2(0.f, 0.f);
+          if (e < ne && i < t.m && kk < kc)
+            av[q] = I.trans ? A[(long long)(k0 + kk) * I.lda + i]
+                            : A[(long long)i * I.lda + k0 + kk];
         }
-        float2 a = make_float2(0.f, 0.f);
-        if (i < t.m && kk < kc)
-          a = I.trans ? A[(long long)(k0 + kk) * I.lda + i] : A[(long long)i * I.lda + k0 + kk];
-        __nv_bfloat16 ar[TC_NS], ai[TC_NS], ni[TC_NS];
-        split3(a.x, ar);
-        split3(a.y, ai);
-        for (int s = 0; s < TC_NS; ++s) ni[s] = __hneg(ai[s]);
-        for (int s = 0; s < TC_NS; ++s) {
-          unsigned char* b = sB + s * B_SLICE_BYTES;
-          *(__nv_bfloat16*)(b + kmaj(2 * i, 2 * kk)) = ar[s];
-          *(__nv_bfloat16*)(b + kmaj(2 * i, 2 * kk + 1)) = ni[s];
-          *(__nv_bfloat16*)(b + kmaj(2 * i + 1, 2 * kk)) = ai[s];
-          *(__nv_bfloat16*)(b + kmaj(2 * i + 1, 2 * kk + 1)) = ar[s];
+#pragma unroll
+        for (int q = 0; q < EMAX; ++q) {
+          const int e = tid + q * TC_THREADS;
+          if (e >= ne) break;
+          int i, kk;
+          if (I.trans) {
+            kk = e / (n_real / 2);
+            i = e % (n_real / 2);
+          } else {
+            i = e / TC_KC;
+            kk = e % TC_KC;
+          }
+          __nv_bfloat16 ar[TC_NS], ai[TC_NS];
+          split3(av[q].x, ar);
+          split3(av[q].y, ai);
+#pragma unroll
+          for (int s = 0; s < TC_NS; ++s) {
+            unsigned char* b = sB + s * B_SLICE_BYTES;
+            *(__nv_bfloat16*)(b + kmaj(2 * i, 2 * kk)) = ar[s];
+            *(__nv_bfloat16*)(b + kmaj(2 * i, 2 * kk + 1)) = __hneg(ai[s]);
+            *(__nv_bfloat16*)(b + kmaj(2 * i + 1, 2 * kk)) = ai[s];
+            *(__nv_bfloat16*)(b + kmaj(2 * i + 1, 2 * kk + 1)) = ar[s];
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;");
@@ -186,8 +218,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gather(const GTask* __restric
       asm volatile("tcgen05.fence::after_thread_sync;");
     }
   }
-  // ---- epilogue: thread (warp w, lane l) owns TMEM lane 32w + l = RHS row
-  if (ok) {
+  // ---- epilogue: thread (warp w < 4, lane l) owns TMEM lane 32w + l = RHS row
+  if (ok && half == 0) {
     const int r = tid;
     const int col = r0 + r;
     float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
