@@ -24,7 +24,10 @@
 // Complex products use the real-expanded block (rows [a_re, -a_im] and
 // [a_im, a_re] over interleaved inner k) as in the mixed-precision engine.
 // One CTA = one task x 128 right-hand sides x 32 complex output rows; one
-// thread issues the MMAs; every mbarrier wait is bounded.
+// thread issues the MMAs; every mbarrier wait is bounded.  Two shared-memory
+// stages alternate: the digits of stage s + 1 are computed while the tensor
+// cores work on stage s; a stage buffer is refilled only after the MMAs that
+// read it have committed.
 #include <cuda_bf16.h>
 
 #include "hm_internal.h"
@@ -44,7 +47,8 @@ constexpr int OZ_WIN = 512;               // complex inner rows per exact window
 constexpr int OZ_THREADS = 256;          // two halves share the digit staging
 constexpr int OZ_A_BYTES = OZ_M * OZ_KR * 2;      // one digit plane of X' (8 KB)
 constexpr int OZ_B_BYTES = OZ_N * OZ_KR * 2;      // one digit plane of B' (4 KB)
-constexpr int OZ_SMEM = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES) + 1024;
+constexpr int OZ_STAGE = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES);   // one pipeline stage (96 KB)
+constexpr int OZ_SMEM = 2 * OZ_STAGE + 1024;                      // double buffered
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -104,16 +108,14 @@ __device__ __forceinline__ void put(float2* p, double2 v) {
 // TX / TY: element type of the input / output panels (complex128 or complex64;
 // complex64 inputs are widened exactly before slicing)
 template <class TX, class TY>
-__global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
     const GTask* __restrict__ tasks, const GItem* __restrict__ items, VBufs vb, ABufs ab,
     int nrhs, const int* __restrict__ task_row_exp, const long long* __restrict__ task_exp_off,
     const int* __restrict__ fexp_in, const int* __restrict__ fexp_far, long long spin_limit,
     int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;                               // OZ_NS digit planes of X'
-  unsigned char* sB = smem + OZ_NS * OZ_A_BYTES;          // OZ_NS digit planes of B'
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int rexp[OZ_RC];
   const GTask t = tasks[blockIdx.x];
@@ -127,9 +129,12 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   const int col = blockIdx.y * OZ_M + row;                // this thread's RHS
   // MMA N: the rows of this CTA, rounded up to 16 (at least 32)
   const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
-  const uint32_t bar = smem_u32(&mbar);
+  const uint32_t bar0 = smem_u32(&mbar[0]);
   if (tid < OZ_RC) rexp[tid] = (tid < nr) ? task_row_exp[task_exp_off[blockIdx.x] + rp + tid] : 0;
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0 + 8));
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_u32(&tmem_base)), "r"(512));
@@ -144,14 +149,28 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
   double acc[OZ_N];
 #pragma unroll
   for (int c = 0; c < OZ_N; ++c) acc[c] = 0.0;
-  uint32_t phase = 0;
+  uint32_t ph[2] = {0u, 0u};
+  bool outstanding[2] = {false, false};   // a committed stage not yet waited for
+  int sidx = 0;                           // pipeline stage counter
   bool ok = true;
   bool fresh = true;        // next MMA of each level starts a new window
   bool pending = false;     // the window holds products not yet added to acc
   int win = 0, cur_buf = -1, F = 0;
 
+  // wait for the MMAs that read stage buffer b (bounded)
+  auto wait_buf = [&](int b) {
+    if (!outstanding[b]) return;
+    if (!mbar_wait(bar0 + 8u * b, ph[b], spin_limit)) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+    }
+    ph[b] ^= 1u;
+    outstanding[b] = false;
+  };
+
   auto flush = [&]() {
-    // all MMAs of the window completed (each stage waited on its commit)
+    wait_buf(0);              // every MMA of the window has completed
+    wait_buf(1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     for (int c0 = 0; owner && c0 < n_real; c0 += 16) {
       long long hi[16], lo[16];
@@ -206,6 +225,10 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
     for (int k0 = 0; k0 < I.k && ok; k0 += OZ_KC) {
       const int kc = min(OZ_KC, I.k - k0);
       if (pending && win + kc > OZ_WIN) flush();
+      const int sb = sidx & 1;
+      wait_buf(sb);           // the stage buffer is free once its previous MMAs committed
+      unsigned char* sA = smem + sb * OZ_STAGE;                  // digit planes of X'
+      unsigned char* sB = sA + OZ_NS * OZ_A_BYTES;               // digit planes of B'
       // ---- X' digits: thread = RHS row, the two halves split the inner rows;
       // all loads of the thread are issued before any use (one memory latency)
       {
@@ -296,20 +319,18 @@ __global__ void __launch_bounds__(OZ_THREADS) k_oz_gather(
           }
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-            :: "r"(bar));
+            :: "r"(bar0 + 8u * sb));
       }
+      outstanding[sb] = true;
+      ++sidx;
       fresh = false;
       pending = true;
       win += kc;
-      if (!mbar_wait(bar, phase, spin_limit)) {
-        ok = false;
-        if (tid == 0) atomicExch(err, 1);
-      }
-      phase ^= 1;
-      asm volatile("tcgen05.fence::after_thread_sync;");
     }
   }
   if (ok && pending) flush();
+  wait_buf(0);                // nothing may still write tensor memory at release
+  wait_buf(1);
   if (ok && owner && col < nrhs) {
     TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
     const TY* base = (t.mode == 1) ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
