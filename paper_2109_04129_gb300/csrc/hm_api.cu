@@ -203,6 +203,122 @@ hm_status row_exponents(hm_ctx* h, const TaskList& tl, RowExp& R) {
   return upload(&R.d_off, R.off, &h->dev_bytes);
 }
 
+// Split the items of one target into split-K tasks (<= KMAX inner rows each),
+// partials into scratch, and add the finalize entry (in place on the target).
+void add_target(hm_ctx* h, TaskList& tl, FinList& fl, int& scr_row, int out_row, int mt,
+                const std::vector<GItem>& its) {
+  if (its.empty()) return;
+  FTask ft{VB_OUT, out_row, mt, VB_OUT, out_row, (int)fl.slots.size(), 0};
+  size_t q = 0;
+  while (q < its.size()) {
+    GTask task{VB_SCR, scr_row, mt, (int)tl.items.size(), 0, 0, 0, 0};
+    long long kk = 0;
+    while (q < its.size() && (kk == 0 || kk + its[q].k <= KMAX)) {
+      tl.items.push_back(its[q]);
+      tl.flops += (long long)mt * its[q].k;
+      tl.a_bytes += (long long)mt * its[q].k * 16;
+      kk += its[q].k;
+      ++q;
+    }
+    task.it1 = (int)tl.items.size();
+    tl.tasks.push_back(task);
+    fl.slots.push_back(scr_row);
+    scr_row += mt;
+  }
+  ft.s1 = (int)fl.slots.size();
+  fl.tasks.push_back(ft);
+}
+
+// Sweep over supernodes: groups of consecutive ranks (nested-dissection
+// separators and bottom groups).  Per group level: (1) every target adds its
+// sources outside its group (alpha blocks, all final), then (2) a multi-leaf
+// group G applies T_G = (I - A_G^T)^-1 (forward) or T_G^T (backward): the
+// within-group substitution as one dense product.  Same result as the leaf
+// substitution; 9 group levels instead of 151 leaf levels on the 2-lambda sphere.
+void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
+  const int n = h->nl;
+  const std::vector<int>& L = h->elim;
+  const int ng = (int)h->grp.size() - 1;
+  std::vector<int> gid(n);
+  for (int g = 0; g < ng; ++g)
+    for (int q = h->grp[g]; q < h->grp[g + 1]; ++q) gid[q] = g;
+  std::vector<std::vector<std::pair<int, long long>>> src(n);
+  for (int k = 0; k < n; ++k) {
+    long long base = h->alpha_row_start[k];
+    for (size_t q = 0; q < h->rows[k].size(); ++q) {
+      int j = h->rows[k][q];
+      if (forward) src[j].push_back({k, base + (long long)q});
+      else src[k].push_back({j, base + (long long)q});
+    }
+  }
+  std::vector<int> glev(ng, 0);
+  int nlev = 0;
+  auto visit = [&](int g) {
+    for (int t = h->grp[g]; t < h->grp[g + 1]; ++t)
+      for (auto& sp : src[t])
+        if (gid[sp.first] != g) glev[g] = std::max(glev[g], glev[gid[sp.first]] + 1);
+    nlev = std::max(nlev, glev[g] + 1);
+  };
+  if (forward) for (int g = 0; g < ng; ++g) visit(g);
+  else for (int g = ng - 1; g >= 0; --g) visit(g);
+  std::vector<std::vector<int>> bylev(nlev);
+  for (int g = 0; g < ng; ++g) bylev[glev[g]].push_back(g);
+  int max_scr = 0;
+  for (int l = 0; l < nlev; ++l) {
+    for (int phase = 0; phase < 2; ++phase) {
+      TaskList tl;
+      FinList fl;
+      int scr_row = 0;
+      for (int g : bylev[l]) {
+        if (phase == 1 && !h->tg_n[g]) continue;
+        const int nG = h->tg_n[g];
+        for (int t = h->grp[g]; t < h->grp[g + 1]; ++t) {
+          const int mt = h->m[L[t]];
+          std::vector<GItem> its;
+          if (phase == 0) {
+            for (auto& sp : src[t]) {
+              if (gid[sp.first] == g) continue;
+              const int s = L[sp.first];
+              GItem it;
+              it.a_off = h->alpha_off[sp.second];
+              it.a_buf = AB_ALPHA;
+              it.lda = forward ? mt : h->m[s];
+              it.trans = forward ? 1 : 0;
+              it.k = h->m[s];
+              it.in_buf = VB_OUT;
+              it.in_row = (int)h->leaf_off[s];
+              its.push_back(it);
+            }
+          } else {
+            const long long T0 = h->tg_off[g];
+            if (forward) {
+              for (int k = h->grp[g]; k < t; ++k)        // T_G(t, k), k before t
+                its.push_back(GItem{T0 + (long long)h->rloc[t] * nG + h->rloc[k], AB_TINV, nG, 0,
+                                    h->m[L[k]], VB_OUT, (int)h->leaf_off[L[k]]});
+            } else {
+              for (int j = t + 1; j < h->grp[g + 1]; ++j)  // T_G(j, t)^T, j after t
+                its.push_back(GItem{T0 + (long long)h->rloc[j] * nG + h->rloc[t], AB_TINV, nG, 1,
+                                    h->m[L[j]], VB_OUT, (int)h->leaf_off[L[j]]});
+            }
+          }
+          add_target(h, tl, fl, scr_row, (int)h->leaf_off[L[t]], mt, its);
+        }
+      }
+      max_scr = std::max(max_scr, scr_row);
+      if (tl.tasks.empty()) continue;
+      sw.part.push_back(std::move(tl));
+      sw.fin.push_back(std::move(fl));
+    }
+  }
+  sw.scratch_rows = max_scr;
+}
+
+bool has_groups(hm_ctx* h) {
+  for (int x : h->tg_n)
+    if (x) return true;
+  return false;
+}
+
 hm_status build_schedules(hm_ctx* h) {
   free_sweep(h->fwd);
   free_sweep(h->bwd);
@@ -219,8 +335,13 @@ hm_status build_schedules(hm_ctx* h) {
   const int n = h->nl;
   size_t* b = &h->dev_bytes;
   if (h->has_scaling) {
-    build_sweep(h, true, h->fwd);
-    build_sweep(h, false, h->bwd);
+    if (has_groups(h)) {
+      build_sweep_groups(h, true, h->fwd);
+      build_sweep_groups(h, false, h->bwd);
+    } else {
+      build_sweep(h, true, h->fwd);
+      build_sweep(h, false, h->bwd);
+    }
     for (int q = 0; q < n; ++q) {
       const int k = h->elim[q];
       GTask t{VB_OUT, (int)h->leaf_off[k], h->m[k], (int)h->dinv_tl.items.size(), 0, 0, 0, 0};
@@ -356,6 +477,7 @@ ABufs abufs(hm_ctx* h) {
   a.p[AB_FAR] = h->d_far;
   a.p[AB_ALPHA] = h->d_alpha;
   a.p[AB_DINV] = h->d_dinv;
+  a.p[AB_TINV] = h->d_tinv;
   return a;
 }
 
@@ -382,6 +504,7 @@ double tl_bytes(const TaskList& tl, int nrhs, double asz = 16, double vsz = 16) 
 namespace hm {
 const void* mixed_alpha(hm_ctx* h);
 const void* mixed_far_data(hm_ctx* h);
+const void* mixed_tinv(hm_ctx* h);
 void* mixed_scratch(hm_ctx* h);
 void* mixed_fart(hm_ctx* h);
 
@@ -398,6 +521,7 @@ static void tables(hm_ctx* h, void* in, void* out, bool low, VBufs& v, ABufs& a)
   a.p[AB_FAR] = low ? mixed_far_data(h) : h->d_far;
   a.p[AB_ALPHA] = low ? mixed_alpha(h) : h->d_alpha;
   a.p[AB_DINV] = h->d_dinv;
+  a.p[AB_TINV] = low ? mixed_tinv(h) : h->d_tinv;
 }
 
 hm_status ensure_err(hm_ctx* h) {
@@ -564,6 +688,7 @@ hm_status upload_values(hm_ctx* h) {
   size_t* b = &h->dev_bytes;
   hm_status s = upload(&h->d_near, h->h_near, b);
   if (!s) s = upload(&h->d_far, h->h_far, b);
+  if (!s) s = upload(&h->d_tinv, h->h_tinv, b);
   if (!s) s = upload(&h->d_alpha, h->h_alpha, b);
   if (!s) s = upload(&h->d_dinv, h->h_dinv, b);
   return s;
@@ -1013,6 +1138,7 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_far);
   cudaFree(h->d_alpha);
   cudaFree(h->d_dinv);
+  cudaFree(h->d_tinv);
   for (int i = 0; i < NPHYS; ++i) cudaFree(h->d_vec[i]);
   cudaFree(h->d_norms);
   cudaFree(h->d_err);

@@ -46,7 +46,7 @@ enum { P_B = 0, P_BO = 1, P_Y = 2, P_Z = 3, P_IT = 4, P_XT = 5, P_R = 6,
        P_X0 = 11, P_B0 = 12,  // FP64 refinement: saved x and b
        NPHYS = 13 };
 // matrix buffers
-enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3 };
+enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3, AB_TINV = 4 };
 
 // A launch-ready list of tasks (device copies of the host vectors).
 struct TaskList {
@@ -107,6 +107,13 @@ struct hm_ctx {
   std::vector<long long> alpha_row_start;  // index of first (k, .) in alpha_off
   std::vector<long long> dinv_off;         // per rank
   std::vector<double> leaf_cen;            // leaf cell centres (built handles)
+  // supernodes (nested-dissection groups of consecutive ranks)
+  std::vector<int> grp;                    // group g = ranks [grp[g], grp[g+1])
+  std::vector<long long> tg_off;           // T_G offset (elements) per group
+  std::vector<int> tg_n;                   // n_G (0: single-leaf group, no T_G)
+  std::vector<int> rloc;                   // rank -> row offset inside its group
+  std::vector<hm::cplx> h_tinv;
+  hm::cplx* d_tinv = nullptr;              // T_G = (I - A_G^T)^-1, row-major
   double wavelength = 1.0, k = 0.0;
   bool has_scaling = false;
   // device data

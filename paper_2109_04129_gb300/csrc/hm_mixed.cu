@@ -31,6 +31,7 @@ enum { Q_B = 0, Q_BO, Q_Y, Q_Z, Q_IT, Q_R, Q_XT, Q_SCR, Q_FAR, NQ };
 struct Mixed {
   float2* alpha = nullptr;
   float2* far = nullptr;
+  float2* tinv = nullptr;
   float2* v[NQ] = {nullptr};
   int cap = 0;
 };
@@ -122,6 +123,7 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   hm_status s = to32(h->h_far, &M->far);
   if (s) return s;
   if (h->has_scaling) s = to32(h->h_alpha, &M->alpha);
+  if (!s && h->has_scaling) s = to32(h->h_tinv, &M->tinv);
   return s;
 }
 
@@ -130,6 +132,7 @@ void hm_mixed_release(hm_ctx* h) {
   if (!M) return;
   dfree(M->alpha);
   dfree(M->far);
+  dfree(M->tinv);
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
   delete M;
   h->mixed = nullptr;
@@ -138,6 +141,7 @@ void hm_mixed_release(hm_ctx* h) {
 namespace hm {
 const void* mixed_alpha(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->alpha : nullptr; }
 const void* mixed_far_data(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->far : nullptr; }
+const void* mixed_tinv(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->tinv : nullptr; }
 void* mixed_scratch(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_SCR] : nullptr; }
 void* mixed_fart(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_FAR] : nullptr; }
 }  // namespace hm

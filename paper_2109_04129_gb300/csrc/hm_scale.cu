@@ -175,6 +175,38 @@ __global__ void __launch_bounds__(512) k_inverse(const cplx* A, int m, cplx* W, 
 
 struct CopyJob { long long src, dst; int rows, cols, trans; };
 
+// identity diagonal blocks of every supernode matrix T_G (row-major n_G x n_G)
+struct EyeJob { long long off; int nG; };
+__global__ void k_eye_groups(const EyeJob* jobs, cplx* T) {
+  EyeJob j = jobs[blockIdx.x];
+  for (int i = threadIdx.x; i < j.nG; i += blockDim.x)
+    T[j.off + (long long)i * j.nG + i] = make_double2(1.0, 0.0);
+}
+
+void k_eye_groups_launch(cplx* dT, const std::vector<long long>& tg_off,
+                         const std::vector<int>& tg_n, const std::vector<int>&,
+                         const std::vector<int>&, const std::vector<int>&) {
+  std::vector<EyeJob> ej;
+  for (size_t g = 0; g < tg_n.size(); ++g)
+    if (tg_n[g]) ej.push_back(EyeJob{tg_off[g], tg_n[g]});
+  if (ej.empty()) return;
+  EyeJob* d = nullptr;
+  if (cudaMalloc((void**)&d, ej.size() * sizeof(EyeJob)) != cudaSuccess) throw HM_ERR_OOM;
+  cudaMemcpy(d, ej.data(), ej.size() * sizeof(EyeJob), cudaMemcpyHostToDevice);
+  k_eye_groups<<<(unsigned)ej.size(), 256>>>(d, dT);
+  cudaDeviceSynchronize();
+  cudaFree(d);
+}
+
+// element offset of alpha_{l j} (ranks, l < j) or -1
+long long zidx_alpha(const std::vector<std::vector<int>>& rows,
+                     const std::vector<long long>& row_start, const std::vector<long long>& aoff,
+                     int l, int j) {
+  auto it = std::lower_bound(rows[l].begin(), rows[l].end(), j);
+  if (it == rows[l].end() || *it != j) return -1;
+  return aoff[row_start[l] + (it - rows[l].begin())];
+}
+
 __global__ void k_copy_blocks(const CopyJob* jobs, const cplx* src, cplx* dst) {
   CopyJob j = jobs[blockIdx.x];
   for (int e = threadIdx.x; e < j.rows * j.cols; e += blockDim.x) {
@@ -223,7 +255,7 @@ __global__ void k_plane_wave(const double* V, const int* T, const double* Q, con
 // statement: median split of the widest axis of the cell centres, ties by
 // leaf number; separator = the first half's leaves adjacent to the second).
 void nd_order(const std::vector<double>& cen, int n, const std::vector<std::pair<int, int>>& near,
-              std::vector<int>& order) {
+              std::vector<int>& order, std::vector<int>* groups = nullptr) {
   std::vector<std::vector<int>> adj(n);
   for (auto& e : near)
     if (e.first != e.second) {
@@ -234,6 +266,7 @@ void nd_order(const std::vector<double>& cen, int n, const std::vector<std::pair
   std::function<void(std::vector<int>)> rec = [&](std::vector<int> ids) {
     if (ids.size() <= 4) {
       std::sort(ids.begin(), ids.end());
+      if (groups && !ids.empty()) groups->push_back((int)order.size());
       order.insert(order.end(), ids.begin(), ids.end());
       return;
     }
@@ -267,6 +300,7 @@ void nd_order(const std::vector<double>& cen, int n, const std::vector<std::pair
     std::sort(S.begin(), S.end());
     rec(A);
     rec(B);
+    if (groups && !S.empty()) groups->push_back((int)order.size());   // the separator
     order.insert(order.end(), S.begin(), S.end());
   };
   std::vector<int> all(n);
@@ -293,13 +327,14 @@ hm_status hm_compute_scaling(hm_handle h) {
     // ---- elimination order
     std::vector<std::pair<int, int>> nearp;
     for (auto& d : h->near) nearp.push_back({d.i, d.j});
-    std::vector<int> elim;
+    std::vector<int> elim, groups;
     if (h->p.ordering == HM_ORDER_ND && (int)h->leaf_cen.size() == 3 * n) {
-      nd_order(h->leaf_cen, n, nearp, elim);
+      nd_order(h->leaf_cen, n, nearp, elim, &groups);
     } else {
       elim.resize(n);
       std::iota(elim.begin(), elim.end(), 0);
     }
+    groups.push_back(n);        // group g = ranks [groups[g], groups[g+1])
     std::vector<int> pos(n);
     for (int q = 0; q < n; ++q) pos[elim[q]] = q;
     // ---- symbolic pattern (ranks)
@@ -439,7 +474,70 @@ hm_status hm_compute_scaling(hm_handle h) {
       cleanup();
       return HM_ERR_SINGULAR;
     }
+    // ---- supernodes: T_G = (I - A_G^T)^-1 for every nested-dissection group G
+    // with more than one leaf (A_G: the alpha blocks inside G), by the
+    // row-block recurrence T_j,: = I_j,: + sum_{l<j in G} alpha_lj^T T_l,:
+    std::vector<long long> tg_off;     // per group: element offset of T_G (n_G x n_G)
+    std::vector<int> tg_n;             // n_G (0 for single-leaf groups)
+    std::vector<int> rloc(n, 0);       // rank -> row offset inside its group
+    long long nt_all = 0;
+    const int ng = (int)groups.size() - 1;
+    for (int g = 0; g < ng; ++g) {
+      int nG = 0;
+      for (int q = groups[g]; q < groups[g + 1]; ++q) { rloc[q] = nG; nG += me[q]; }
+      bool multi = groups[g + 1] - groups[g] > 1;
+      tg_off.push_back(nt_all);
+      tg_n.push_back(multi ? nG : 0);
+      if (multi) nt_all += (long long)nG * nG;
+    }
+    cplx* dT = nullptr;
+    if (nt_all > 0) {
+      HM_CUDA(cudaMalloc((void**)&dT, nt_all * sizeof(cplx)));
+      HM_CUDA(cudaMemset(dT, 0, nt_all * sizeof(cplx)));
+      std::vector<cplx> eye_dummy;
+      // identity diagonal blocks
+      std::vector<CopyJob> ij;
+      int maxg = 0;
+      for (int g = 0; g < ng; ++g) {
+        if (!tg_n[g]) continue;
+        maxg = std::max(maxg, groups[g + 1] - groups[g]);
+      }
+      k_eye_groups_launch(dT, tg_off, tg_n, groups, rloc, me);
+      for (int pr = 1; pr < maxg; ++pr) {
+        for (int qr = 0; qr < pr; ++qr) {
+          std::vector<BTask> bt;
+          for (int g = 0; g < ng; ++g) {
+            if (!tg_n[g] || groups[g] + pr >= groups[g + 1]) continue;
+            const int j = groups[g] + pr, l = groups[g] + qr;
+            long long a = zidx_alpha(rows, row_start, aoff, l, j);
+            if (a < 0) continue;
+            const int nG = tg_n[g];
+            const int w = rloc[l] + me[l];         // columns 0 .. (end of block l)
+            cplx* base = dT + tg_off[g];
+            bt.push_back(BTask{dA + a, base + (long long)rloc[l] * nG, base + (long long)rloc[j] * nG,
+                               me[j], w, me[l], me[j], nG, nG, 1, 1, 1.0});
+          }
+          if (bt.empty()) continue;
+          BTask* dbt = nullptr;
+          HM_CUDA(cudaMalloc((void**)&dbt, bt.size() * sizeof(BTask)));
+          HM_CUDA(cudaMemcpy(dbt, bt.data(), bt.size() * sizeof(BTask), cudaMemcpyHostToDevice));
+          k_bgemm<<<(unsigned)bt.size(), 256>>>(dbt);
+          cudaError_t ce = cudaDeviceSynchronize();
+          cudaFree(dbt);
+          if (ce != cudaSuccess) throw cuda_status(ce);
+        }
+      }
+    }
     // ---- install
+    cudaFree(h->d_tinv);
+    h->d_tinv = dT;
+    h->grp = groups;
+    h->tg_off = tg_off;
+    h->tg_n = tg_n;
+    h->rloc = rloc;
+    h->h_tinv.resize(nt_all);
+    if (nt_all)
+      HM_CUDA(cudaMemcpy(h->h_tinv.data(), dT, nt_all * sizeof(cplx), cudaMemcpyDeviceToHost));
     cudaFree(h->d_alpha);
     cudaFree(h->d_dinv);
     h->d_alpha = dA;
