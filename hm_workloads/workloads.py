@@ -96,6 +96,11 @@ WORKLOADS = {
 
 
 def get_workload(name: str) -> Workload:
+    """A named workload, or member s of the seeded scatterer batch as
+    ``scatterer_<s>``."""
+    if name.startswith("scatterer_") and name[10:].isdigit():
+        s = int(name[10:])
+        return scatterer_batch(s + 1)[s]
     return WORKLOADS[name]
 
 
@@ -113,10 +118,9 @@ def scatterer_batch(count: int = 64, wavelength: float = 1.0):
         leaf = int(rng.choice([32, 64, 128, 256]))
         kind = s % 3
         if kind == 0 or kind == 1:
-            # icosphere level giving >= target/4 unknowns, then radius for edge h
-            level = 2
-            while 30 * 4 ** level < target and level < 6:
-                level += 1
+            # icosphere level whose unknown count 30 * 4^level is nearest the
+            # target in log scale (1920, 7680 or 30720), then radius for edge h
+            level = min(5, max(3, int(round(math.log(target / 30.0, 4)))))
             ntri = 20 * 4 ** level
             area = ntri * (math.sqrt(3) / 4) * h * h
             if kind == 0:

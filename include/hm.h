@@ -136,6 +136,28 @@ hm_status hm_apply(hm_handle h, int op, void* Y, const void* X, int nrhs);
 hm_status hm_plane_wave_rhs(hm_handle h, const double* theta_host, const double* phi_host,
                             const int* pol_host, int nrhs, void* B);
 
+/* Grouped solve of many independent problems (a batch of scatterers, each
+ * with its own handle, H-matrix and scaling): for every i < count,
+ * X[i] = solve(hs[i], B[i], nrhs[i]) exactly as hm_power_series_solve does
+ * (Eq. 25-36 per problem; the paper's method is per scatterer, and a batch is
+ * a set of independent runs of it).  X[i], B[i]: device, N_i x nrhs[i]
+ * complex128, original order, owned by the caller; the handles must be
+ * distinct, scaled, and not profiling.  The first call for a given list of
+ * (handle, X, B, nrhs) runs one ordinary solve per problem on the first
+ * handle's stream and waits for it, then records all of them into one CUDA
+ * graph with one branch per problem and keeps the instantiated graph; every
+ * call, the first included, then launches that graph on the first handle's
+ * stream (asynchronous).  Returns HM_ERR_INVALID for null or repeated handles
+ * or non-positive counts, HM_ERR_STATE for a handle without scaling or with
+ * profiling on, and the first failing solve's status otherwise.  A kept graph is
+ * rebuilt when a handle's device buffers or schedules have been replaced
+ * since it was recorded, and dropped when one of its handles is destroyed.
+ * While it runs, a branch uses its handle's work panels: do not run other
+ * work on those handles until the stream has reached the graph's end.
+ * Diagnostics per handle come from hm_get_diagnostics as usual. */
+hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, const int* nrhs,
+                           int count);
+
 hm_status hm_set_stream(hm_handle h, void* cuda_stream);
 hm_status hm_num_unknowns(hm_handle h, int* n);
 

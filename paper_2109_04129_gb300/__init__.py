@@ -33,7 +33,7 @@ SYMBOLS = ("hm_default_params", "hm_build", "hm_import", "hm_save", "hm_compute_
            "hm_power_series_solve", "hm_power_series_solve_host", "hm_apply",
            "hm_plane_wave_rhs", "hm_set_stream", "hm_num_unknowns", "hm_get_diagnostics",
            "hm_get_stats", "hm_get_tree", "hm_destroy", "hm_status_string",
-           "hm_profile_enable", "hm_get_profile", "hm_apply_far_noalloc")
+           "hm_profile_enable", "hm_get_profile", "hm_apply_far_noalloc", "hm_solve_grouped")
 PROF_CATEGORIES = ("rt_sweep", "r_sweep", "sweep_finalize", "dinv", "far_stage1",
                    "far_stage2", "near", "misc", "mixed_sweep", "mixed_far", "conversion")
 
@@ -71,6 +71,7 @@ for name, args in {
     "hm_profile_enable": [_vp, _i],
     "hm_get_profile": [_vp, _P(_d), _i],
     "hm_apply_far_noalloc": [_vp, _vp, _vp, _i],
+    "hm_solve_grouped": [_P(_vp), _P(_vp), _P(_vp), _P(_i), _i],
 }.items():
     fn = getattr(_lib, name)
     fn.argtypes = args
@@ -234,6 +235,26 @@ class Solver:
         _check(_lib.hm_get_tree(self._h, perm.ctypes.data_as(_P(ctypes.c_longlong)),
                                 off.ctypes.data_as(_P(ctypes.c_longlong))), "hm_get_tree")
         return perm, off
+
+
+def solve_grouped(solvers, Xs, Bs):
+    """Grouped solve of independent problems: Xs[i] <- solve of solvers[i] for
+    Bs[i] (tensors as in Solver.solve), recorded once into one CUDA graph with
+    a branch per problem and replayed on torch's current stream."""
+    n = len(solvers)
+    if n == 0 or len(Xs) != n or len(Bs) != n:
+        raise ValueError("need one X and one B per solver")
+    for s, X, B in zip(solvers, Xs, Bs):
+        Solver._panel_ok(X, s.N)
+        Solver._panel_ok(B, s.N)
+        if X.shape != B.shape:
+            raise ValueError("X and B shapes differ")
+    solvers[0]._stream()
+    hs = (_vp * n)(*[s._h.value for s in solvers])
+    xs = (_vp * n)(*[X.data_ptr() for X in Xs])
+    bs = (_vp * n)(*[B.data_ptr() for B in Bs])
+    nr = (_i * n)(*[B.shape[0] for B in Bs])
+    return _check(_lib.hm_solve_grouped(hs, xs, bs, nr, n), "hm_solve_grouped")
 
 
 def exported_symbols():

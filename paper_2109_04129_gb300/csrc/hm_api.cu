@@ -444,11 +444,13 @@ hm_status build_schedules(hm_ctx* h) {
   if (!s && h->has_scaling) s = row_exponents(h, h->dinv_tl, h->rexp_dinv);
   if (s) return s;
   h->sched_ready = true;
+  ++h->gen;
   return HM_OK;
 }
 
 hm_status ensure_buffers(hm_ctx* h, int nrhs) {
   if (nrhs <= h->cap_nrhs) return HM_OK;
+  ++h->gen;
   for (int i = 0; i < NPHYS; ++i) {
     cudaFree(h->d_vec[i]);
     h->d_vec[i] = nullptr;
@@ -1125,6 +1127,7 @@ hm_status hm_get_profile(hm_handle h, double* out, int ncat) {
 
 hm_status hm_destroy(hm_handle h) {
   if (!h) return HM_OK;
+  hm::hm_group_forget(h);
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   free_sweep(h->fwd);
   free_sweep(h->bwd);

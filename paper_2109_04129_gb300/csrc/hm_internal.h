@@ -88,6 +88,7 @@ struct FarDesc {
 };
 struct NearDesc { int i, j; long long off; };
 
+void hm_group_forget(hm_ctx* h);   // drops grouped-solve graphs that use h
 }  // namespace hm
 
 struct hm_ctx {
@@ -157,6 +158,9 @@ struct hm_ctx {
   size_t evused = 0;
   std::vector<double> ratio, resid;
   size_t dev_bytes = 0;
+  // bumped whenever device buffers or task lists are replaced; a grouped-solve
+  // graph captured under another value refers to freed memory and is rebuilt
+  unsigned long long gen = 0;
 };
 
 namespace hm {

@@ -54,6 +54,7 @@ hm_status to32(const std::vector<cplx>& src, float2** dst) {
 
 hm_status ensure32(hm_ctx* h, Mixed* M, int nrhs) {
   if (nrhs <= M->cap) return HM_OK;
+  ++h->gen;
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
   M->cap = 0;
   for (int i = 0; i < NQ; ++i) {
@@ -115,6 +116,7 @@ hm_status series32(hm_ctx* h, Mixed* M, int nrhs, bool diag) {
 
 hm_status hm_mixed_prepare(hm_ctx* h) {
   if (h->p.precision != HM_MIXED) return HM_OK;
+  ++h->gen;
   Mixed* M = (Mixed*)h->mixed;
   if (!M) {
     M = new Mixed();

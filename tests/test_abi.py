@@ -53,3 +53,8 @@ def test_null_arguments_rejected(lib):
     assert lib.hm_destroy(None) == hp.HM_OK
     h = ctypes.c_void_p()
     assert lib.hm_import(None, None, ctypes.byref(h)) == hp.HM_ERR_INVALID
+    assert lib.hm_solve_grouped(None, None, None, None, 1) == hp.HM_ERR_INVALID
+    arr = (ctypes.c_void_p * 1)(None)
+    nr = (ctypes.c_int * 1)(1)
+    assert lib.hm_solve_grouped(arr, arr, arr, nr, 1) == hp.HM_ERR_INVALID
+    assert lib.hm_solve_grouped(arr, arr, arr, nr, 0) == hp.HM_ERR_INVALID
