@@ -74,8 +74,13 @@ hm_status upload_fin(FinList& fl, size_t* bytes) {
 void free_tasks(TaskList& tl) {
   cudaFree(tl.d_tasks);
   cudaFree(tl.d_items);
+  cudaFree(tl.d_tiles);
+  cudaFree(tl.d_toff);
   tl.d_tasks = nullptr;
   tl.d_items = nullptr;
+  tl.d_tiles = nullptr;
+  tl.d_toff = nullptr;
+  tl.tile_bytes = 0;
 }
 void free_sweep(Sweep& sw) {
   for (auto& t : sw.part) free_tasks(t);
@@ -469,6 +474,14 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
   HM_CUDA(cudaMalloc((void**)&h->d_norms, 4 * sizeof(double) * nrhs));
   cudaFree(h->d_fexp);
   HM_CUDA(cudaMalloc((void**)&h->d_fexp, 2 * sizeof(int) * nrhs));
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(h->d_xdig[i]);
+    h->d_xdig[i] = nullptr;
+  }
+  if (h->p.precision == HM_MIXED && h->p.fp64_emulation) {
+    HM_CUDA(cudaMalloc((void**)&h->d_xdig[0], oz_panel_bytes(h->N, nrhs)));
+    HM_CUDA(cudaMalloc((void**)&h->d_xdig[1], oz_panel_bytes(std::max(1, h->far_t_rows), nrhs)));
+  }
   h->cap_nrhs = nrhs;
   return HM_OK;
 }
@@ -588,8 +601,15 @@ hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, i
   ABufs a;
   tables(h, in, out, false, v, a);
   int ev = prof_begin(h);
+  OzPanels xp;
+  xp.xd[0] = h->d_xdig[0];
+  xp.xd[1] = h->d_xdig[1];
+  xp.J[0] = oz_row_groups(h->N);
+  xp.J[1] = oz_row_groups(std::max(1, h->far_t_rows));
+  xp.G = oz_rhs_groups(h->cap_nrhs);
+  if (!xp.xd[0] || !xp.xd[1]) return HM_ERR_STATE;
   s = launch_tasks_oz(tl, v, a, nrhs, h->stream, R.d_e, R.d_off, h->d_fexp,
-                      h->d_fexp + h->cap_nrhs, h->p.spin_limit, h->d_err, panels32);
+                      h->d_fexp + h->cap_nrhs, xp, h->p.spin_limit, h->d_err, panels32);
   prof_end(h, ev, cat, tl_bytes(tl, nrhs, 16, panels32 ? 8 : 16), 8.0 * tl.flops * nrhs);
   return s;
 }
@@ -1146,6 +1166,8 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_norms);
   cudaFree(h->d_err);
   cudaFree(h->d_fexp);
+  cudaFree(h->d_xdig[0]);
+  cudaFree(h->d_xdig[1]);
   for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2, &h->rexp_dinv}) {
     cudaFree(R->d_e);
     cudaFree(R->d_off);

@@ -56,6 +56,11 @@ struct TaskList {
   GItem* d_items = nullptr;
   long long flops = 0;    // complex MACs per RHS
   long long a_bytes = 0;  // matrix bytes read per launch
+  // tensor-core path: the complex64 matrix operand of every stage pre-split
+  // into bf16 tiles (hm_tc.cu), task t's tiles from byte d_toff[t]
+  unsigned char* d_tiles = nullptr;
+  long long* d_toff = nullptr;
+  size_t tile_bytes = 0;
 };
 // per-task row scale exponents of a task list (FP64-accurate tensor products)
 struct RowExp {
@@ -151,6 +156,7 @@ struct hm_ctx {
   int* d_err = nullptr;         // device status word (bounded waits that timed out)
   hm::RowExp rexp_near, rexp_far1, rexp_far2, rexp_dinv;
   int* d_fexp = nullptr;        // 2 * cap_nrhs column exponents
+  unsigned char* d_xdig[2] = {nullptr, nullptr};   // digit panels (OzPanels)
   // profiling (hm_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> evpool;
@@ -182,12 +188,27 @@ bool tc_ok_for(const TaskList& tl);
 // hm_oz.cu: FP64-accurate products on tensor cores
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s);
 hm_status launch_col_exp32(const float2* V, int rows, int nrhs, int* out, cudaStream_t s);
+// Digit panels of the inputs of the FP64-accurate products: eight planes of
+// signed 7-bit digits of a vector panel, tiled exactly as the MMA reads them
+// from shared memory (xd[0]: the VB_IN input, xd[1]: the VB_FAR input).
+struct OzPanels {
+  const unsigned char* xd[2];
+  long long J[2];   // 4-row groups of each panel
+  int G;            // 8-RHS groups of both panels
+};
+long long oz_row_groups(int rows);
+int oz_rhs_groups(int nrhs);
+size_t oz_panel_bytes(int rows, int nrhs);
+hm_status launch_digitize(const void* V, bool f32, int rows, int nrhs, const int* fexp,
+                          unsigned char* out, long long J, int G, cudaStream_t s);
 hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, const int* row_exp, const long long* exp_off,
-                          const int* fexp_in, const int* fexp_far, long long spin_limit,
-                          int* err, bool panels32 = false);
+                          const int* fexp_in, const int* fexp_far, const OzPanels& xp,
+                          long long spin_limit, int* err, bool panels32 = false);
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, long long spin_limit, int* err);
+// pre-split the complex64 matrix operand of a tensor-core task list (set-up)
+hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s);
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,

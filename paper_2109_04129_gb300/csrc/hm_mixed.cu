@@ -78,6 +78,8 @@ hm_status copy32(hm_ctx* h, float2* d, const float2* s, int nrhs) {
 hm_status dinv32(hm_ctx* h, float2* in, float2* out, int nrhs) {
   if (h->p.fp64_emulation && nrhs >= 32) {
     hm_status s = launch_col_exp32(in, h->N, nrhs, h->d_fexp, h->stream);
+    if (!s) s = launch_digitize(in, true, h->N, nrhs, h->d_fexp, h->d_xdig[0],
+                                oz_row_groups(h->N), oz_rhs_groups(h->cap_nrhs), h->stream);
     if (s) return s;
     return run_oz_list(h, h->dinv_tl, h->rexp_dinv, in, out, nrhs, PC_DINV, true);
   }
@@ -126,7 +128,17 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   if (s) return s;
   if (h->has_scaling) s = to32(h->h_alpha, &M->alpha);
   if (!s && h->has_scaling) s = to32(h->h_tinv, &M->tinv);
-  return s;
+  if (s || !h->p.tensor_cores) return s;
+  // bf16 slices of every complex64 matrix operand of the tensor-core lists
+  ABufs a{};
+  a.p[AB_FAR] = M->far;
+  a.p[AB_ALPHA] = M->alpha;
+  a.p[AB_TINV] = M->tinv;
+  for (Sweep* sw : {&h->fwd, &h->bwd})
+    for (TaskList& tl : sw->part)
+      if ((s = build_tc_tiles(tl, a, &h->dev_bytes))) return s;
+  if ((s = build_tc_tiles(h->far1_tl, a, &h->dev_bytes))) return s;
+  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes);
 }
 
 void hm_mixed_release(hm_ctx* h) {
@@ -154,14 +166,21 @@ static hm_status residual_products(hm_ctx* h, int nrhs, bool with_far) {
   cplx** V = h->d_vec;
   hm_status s;
   if (h->p.fp64_emulation && nrhs >= 32) {
+    const int G = oz_rhs_groups(h->cap_nrhs);
     if ((s = launch_col_exp(V[P_XT], h->N, nrhs, h->d_fexp, h->stream))) return s;
+    if ((s = launch_digitize(V[P_XT], false, h->N, nrhs, h->d_fexp, h->d_xdig[0],
+                             oz_row_groups(h->N), G, h->stream)))
+      return s;
     if ((s = run_oz_list(h, h->near_tl, h->rexp_near, V[P_XT], V[P_Y], nrhs, PC_NEAR)))
       return s;
     if (!with_far) return HM_OK;
     if ((s = run_oz_list(h, h->far1_tl, h->rexp_far1, V[P_XT], nullptr, nrhs, PC_FAR1)))
       return s;
-    if ((s = launch_col_exp(h->d_vec[P_FAR], std::max(1, h->far_t_rows), nrhs,
-                            h->d_fexp + h->cap_nrhs, h->stream)))
+    const int tr = std::max(1, h->far_t_rows);
+    if ((s = launch_col_exp(h->d_vec[P_FAR], tr, nrhs, h->d_fexp + h->cap_nrhs, h->stream)))
+      return s;
+    if ((s = launch_digitize(h->d_vec[P_FAR], false, tr, nrhs, h->d_fexp + h->cap_nrhs,
+                             h->d_xdig[1], oz_row_groups(tr), G, h->stream)))
       return s;
     return run_oz_list(h, h->far2_tl, h->rexp_far2, V[P_XT], V[P_Z], nrhs, PC_FAR2);
   }
