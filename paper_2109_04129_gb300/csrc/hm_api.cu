@@ -76,6 +76,9 @@ void free_tasks(TaskList& tl) {
   cudaFree(tl.d_items);
   cudaFree(tl.d_tiles);
   cudaFree(tl.d_toff);
+  cudaFree(tl.d_units);
+  tl.d_units = nullptr;
+  tl.n_units = 0;
   tl.d_tasks = nullptr;
   tl.d_items = nullptr;
   tl.d_tiles = nullptr;
@@ -447,6 +450,8 @@ hm_status build_schedules(hm_ctx* h) {
   if (!s) s = row_exponents(h, h->far1_tl, h->rexp_far1);
   if (!s) s = row_exponents(h, h->far2_tl, h->rexp_far2);
   if (!s && h->has_scaling) s = row_exponents(h, h->dinv_tl, h->rexp_dinv);
+  for (TaskList* tl : {&h->near_tl, &h->far1_tl, &h->far2_tl, &h->dinv_tl})
+    if (!s) s = build_oz_units(*tl, &h->dev_bytes);
   if (s) return s;
   h->sched_ready = true;
   ++h->gen;

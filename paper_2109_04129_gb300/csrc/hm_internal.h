@@ -61,6 +61,9 @@ struct TaskList {
   unsigned char* d_tiles = nullptr;
   long long* d_toff = nullptr;
   size_t tile_bytes = 0;
+  // FP64-accurate path: work units (task, 32-row pass), costliest first
+  int2* d_units = nullptr;
+  int n_units = 0;
 };
 // per-task row scale exponents of a task list (FP64-accurate tensor products)
 struct RowExp {
@@ -196,6 +199,7 @@ struct OzPanels {
   long long J[2];   // 4-row groups of each panel
   int G;            // 8-RHS groups of both panels
 };
+hm_status build_oz_units(TaskList& tl, size_t* dev_bytes);
 long long oz_row_groups(int rows);
 int oz_rhs_groups(int nrhs);
 size_t oz_panel_bytes(int rows, int nrhs);

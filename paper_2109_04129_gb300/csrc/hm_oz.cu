@@ -25,23 +25,32 @@
 // Complex products use the real-expanded block (rows [a_re, -a_im] and
 // [a_im, a_re] over interleaved inner k) as in the mixed-precision engine.
 //
-// The input panel is sliced once per product by k_digitize into eight digit
-// planes that are already tiled like the MMA's shared-memory operand (8 RHS x
-// 8 real inner core matrices of 128 bytes, 4-row groups contiguous), so a
-// pipeline stage fetches its 128 RHS x 16 complex rows with 128 bulk copies
-// of 512 bytes (cp.async.bulk, completion on an mbarrier) and no arithmetic.
-// The matrix side (32 complex output rows x 16 inner rows per stage) is
-// sliced on the fly from FP64, its loads issued one stage ahead.  A stage
-// starts on a 4-row boundary of the panel (bulk copies need 16-byte aligned
-// sources): the inner rows that the shift brings in before or after an item
+// Data movement.  The input panel is sliced once per product by k_digitize
+// into eight digit planes tiled so that the operand of one pipeline stage
+// (128 right-hand sides x 8 complex inner rows of one plane) is one
+// contiguous 4 KB block in the MMA's shared-memory layout: a stage arrives
+// with eight bulk copies (cp.async.bulk, completion on an mbarrier).  The
+// matrix side (32 complex output rows x 8 inner rows per stage) is sliced on
+// the fly from FP64.  A stage starts on a 4-row boundary of the panel (bulk
+// copies need 16-byte aligned sources): the inner rows the shift brings in
 // meet zero matrix digits and add exact zeros.
 //
-// One CTA = one task x 128 right-hand sides x 32 complex output rows; one
-// thread issues the MMAs; every mbarrier wait is bounded and a failed wait is
-// made uniform across the CTA before any decision that depends on it.  Two
-// shared-memory stages alternate; a stage buffer is refilled only after the
-// MMAs that read it have committed.
+// Kernel organisation (persistent, warp-specialised, one CTA per SM).  A work
+// unit is (task, 32-row pass); each CTA walks its share of the units,
+// costliest first, for one tile of 128 right-hand sides.  Warp 1 issues the
+// bulk copies, warps 2-3 slice the matrix digits, warp 0 (one thread) issues
+// the 36 MMAs of a stage, warps 4-7 read the level accumulators out of tensor
+// memory and keep the FP64 sums.  They hand over through mbarriers: a ring of
+// four shared-memory stages (full: copies landed; digits: matrix digits
+// written; empty: the MMAs that read it completed) and the tensor-memory
+// window (full: the window's MMAs completed; empty: the epilogue has read it).
+// Every wait is bounded and watches a CTA-wide abort flag; a CTA that gives up
+// records it in *err, lets its copies and MMAs finish (bounded, with a limit
+// of its own) and releases tensor memory.
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "hm_internal.h"
 
@@ -49,47 +58,60 @@ namespace hm {
 
 namespace {
 
-constexpr int OZ_M = 128;                 // RHS per CTA
-constexpr int OZ_KC = 16;                 // complex inner rows per stage
-constexpr int OZ_KR = 32;                 // real inner columns per stage
+constexpr int OZ_M = 128;                 // RHS per CTA tile (MMA M)
+constexpr int OZ_KC = 8;                  // complex inner rows per stage
+constexpr int OZ_KR = 16;                 // real inner columns per stage (one MMA K)
 constexpr int OZ_NS = 8;                  // digits per value
 constexpr int OZ_LV = 8;                  // levels kept (p + q <= 7)
-constexpr int OZ_RC = 32;                 // complex output rows per CTA
-constexpr int OZ_N = 64;                  // MMA N (2 * OZ_RC)
+constexpr int OZ_RC = 32;                 // complex output rows per unit
+constexpr int OZ_N = 64;                  // MMA N columns reserved per level (2 * OZ_RC)
 constexpr int OZ_WIN = 256;               // complex inner rows per exact window
 constexpr int OZ_THREADS = 256;
-constexpr int OZ_A_BYTES = OZ_M * OZ_KR * 2;      // one digit plane of X' (8 KB)
-constexpr int OZ_B_BYTES = OZ_N * OZ_KR * 2;      // one digit plane of B' (4 KB)
-constexpr int OZ_STAGE = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES);   // one pipeline stage (96 KB)
-constexpr int OZ_SMEM = 2 * OZ_STAGE + 1024;                      // double buffered
-constexpr int OZ_COPY = 512;              // one bulk copy: 8 RHS x 16 complex rows, one plane
-constexpr int OZ_COPIES = OZ_NS * (OZ_M / 8);                     // 128 per stage
+constexpr int OZ_RING = 4;                // shared-memory stages
+constexpr int OZ_BPROD = 64;              // matrix-digit producer threads (warps 2-3)
+constexpr int OZ_A_BYTES = OZ_M * OZ_KR * 2;      // one digit plane of X' (4 KB)
+constexpr int OZ_B_BYTES = OZ_N * OZ_KR * 2;      // one digit plane of B' (2 KB)
+constexpr int OZ_STAGE = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES);   // 48 KB
+constexpr int OZ_SMEM = OZ_RING * OZ_STAGE + 1024;
+constexpr int OZ_GROUP = 16 * 128;       // one 4-row group of a 128-RHS tile, one plane (2 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ uint32_t kmaj(int row, int k) {
+// B' (matrix) tile: canonical K-major, 8-row groups of (OZ_KR / 8) core matrices
+__device__ __forceinline__ uint32_t kmaj_b(int row, int k) {
   return ((row >> 3) * (OZ_KR >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+// shared-memory matrix descriptor (no swizzle): lbo = byte distance of
+// K-adjacent core matrices, sbo = byte distance of adjacent 8-row groups
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)(((OZ_KR / 8) * 128u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit) {
-  uint32_t done = 0;
+
+// bounded wait that also gives up when another role has aborted the CTA
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t phase, long long limit,
+                                        volatile int* abort_flag, int* err) {
   for (long long it = 0; it < limit; ++it) {
+    uint32_t done = 0;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(bar), "r"(phase));
     if (done) return true;
+    if (*abort_flag) return false;
   }
+  *abort_flag = 1;
+  atomicExch(err, 1);
   return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
 // Eight balanced base-128 digits of trunc(v 2^(55 - S)) for |v| < 2^S
@@ -124,18 +146,28 @@ __device__ __forceinline__ void digits(double v, int S, __nv_bfloat16* d) {
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
-
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ void put(double2* p, double2 v) { *p = v; }
 __device__ __forceinline__ void put(float2* p, double2 v) {
   *p = make_float2((float)v.x, (float)v.y);
 }
+// 2^e as a double (exact; ldexp outside the normal range)
+__device__ __forceinline__ double pow2i(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                   : ldexp(1.0, e);
+}
 
-// byte offset of core matrix (plane p, RHS group g, 4-row group j) in a panel
-__host__ __device__ __forceinline__ long long xd_off(int p, int G, long long g, long long J,
-                                                     long long j) {
-  return (((long long)p * G + g) * J + j) * 128;
+// byte offset of the 16-byte row (plane p, 128-RHS tile y, 4-row group j,
+// 8-RHS group gl, RHS r8 within it) of a digit panel with Y tiles and J groups
+__host__ __device__ __forceinline__ long long xd_off(int p, int Y, int y, long long J, long long j,
+                                                     int gl, int r8) {
+  return ((((long long)p * Y + y) * J + j) * 16 + gl) * 128 + r8 * 16;
+}
+
+// stages of an item: 8-row stages from the 4-row boundary below its first row
+__host__ __device__ __forceinline__ int oz_nst(const GItem& I) {
+  return (I.k + (I.in_row & 3) + OZ_KC - 1) / OZ_KC;
 }
 
 // Digit panel of V (rows x nrhs, RHS fastest; complex128 or complex64 widened
@@ -164,6 +196,7 @@ __global__ void k_digitize(const TV* __restrict__ V, int rows, int nrhs,
     digits(v[c].x, F, d[2 * c]);
     digits(v[c].y, F, d[2 * c + 1]);
   }
+  const int Y = G / 16;
 #pragma unroll
   for (int p = 0; p < OZ_NS; ++p) {
     uint4 w;
@@ -171,38 +204,47 @@ __global__ void k_digitize(const TV* __restrict__ V, int rows, int nrhs,
     w.y = pack2(d[2][p], d[3][p]);
     w.z = pack2(d[4][p], d[5][p]);
     w.w = pack2(d[6][p], d[7][p]);
-    *(uint4*)(out + xd_off(p, G, r >> 3, J, j) + (r & 7) * 16) = w;
+    *(uint4*)(out + xd_off(p, Y, r >> 7, J, j, (r >> 3) & 15, r & 7)) = w;
   }
 }
 
 // TY: element type of the output (and base) panels
 template <class TY>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
-    const GTask* __restrict__ tasks, const GItem* __restrict__ items, VBufs vb, ABufs ab,
-    int nrhs, const int* __restrict__ task_row_exp, const long long* __restrict__ task_exp_off,
+    const GTask* __restrict__ tasks, const GItem* __restrict__ items,
+    const int2* __restrict__ units, int n_units, VBufs vb, ABufs ab, int nrhs,
+    const int* __restrict__ task_row_exp, const long long* __restrict__ task_exp_off,
     const int* __restrict__ fexp_in, const int* __restrict__ fexp_far, OzPanels xp,
     long long spin_limit, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t mbar[4];   // [b]: MMAs of buffer b done; [2 + b]: its copies landed
+  __shared__ __align__(8) uint64_t bars[3 * OZ_RING + 3];
   __shared__ uint32_t tmem_base;
-  __shared__ int rexp[OZ_RC];
-  const GTask t = tasks[blockIdx.x];
-  const int rp = blockIdx.z * OZ_RC;                      // first complex row of this CTA
-  if (rp >= t.m) return;                                  // whole CTA: uniform
-  const int nr = min(OZ_RC, t.m - rp);
+  __shared__ int abort_flag;
+  __shared__ int armed_s, consumed_s;     // stages armed by the copy warp / taken by the MMA warp
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row = tid & (OZ_M - 1);                       // RHS row (TMEM lane) of this thread
-  const bool owner = tid < OZ_M;                          // warps 0-3 read TMEM, own acc
-  const int col = blockIdx.y * OZ_M + row;                // this thread's RHS
-  // MMA N: the rows of this CTA, rounded up to 16 (at least 32)
-  const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
-  const uint32_t bar_done = smem_u32(&mbar[0]);
-  const uint32_t bar_full = smem_u32(&mbar[2]);
-  if (tid < OZ_RC) rexp[tid] = (tid < nr) ? task_row_exp[task_exp_off[blockIdx.x] + rp + tid] : 0;
+  const uint32_t b_full = smem_u32(&bars[0]);             // + 8 b: copies of stage b landed
+  const uint32_t b_digs = smem_u32(&bars[OZ_RING]);       // + 8 b: matrix digits of b written
+  const uint32_t b_empty = smem_u32(&bars[2 * OZ_RING]);  // + 8 b: MMAs reading b completed
+  const uint32_t b_tfull = smem_u32(&bars[3 * OZ_RING]);
+  const uint32_t b_tempty = b_tfull + 8;
+  const uint32_t b_fin = b_tfull + 16;
+  volatile int* abortp = &abort_flag;
+  const int y = blockIdx.y;
+  const int Y = xp.G / 16;
   if (tid == 0) {
-    for (int b = 0; b < 4; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_done + 8u * b));
+    for (int b = 0; b < OZ_RING; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_full + 8u * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_digs + 8u * b),
+                   "r"(OZ_BPROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_empty + 8u * b));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tfull));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_tempty), "r"(OZ_M));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_fin));
+    abort_flag = 0;
+    armed_s = 0;
+    consumed_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -214,222 +256,307 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_real >> 3) << 17) |
-                         ((uint32_t)(OZ_M >> 4) << 24);
-  double acc[OZ_N];
-#pragma unroll
-  for (int c = 0; c < OZ_N; ++c) acc[c] = 0.0;
-  uint32_t ph_done[2] = {0u, 0u}, ph_full[2] = {0u, 0u};
-  bool outstanding[2] = {false, false};   // MMAs committed on buffer b, not yet waited for
-  bool landing[2] = {false, false};       // copies issued into buffer b, not yet waited for
-  int sidx = 0;                           // pipeline stage counter
-  bool fail = false;        // this thread saw a wait run out (sticky)
-  bool ok = true;           // no thread has: uniform, refreshed at every CTA barrier
-  bool fresh = true;        // next MMA of each level starts a new window
-  bool pending = false;     // the window holds products not yet added to acc
-  int win = 0, cur_buf = -1, F = 0;
 
-  // wait for the MMAs that read stage buffer b (bounded)
-  auto wait_buf = [&](int b) {
-    if (!outstanding[b]) return;
-    if (!mbar_wait(bar_done + 8u * b, ph_done[b], spin_limit)) {
-      fail = true;
-      if (tid == 0) atomicExch(err, 1);
-    }
-    ph_done[b] ^= 1u;
-    outstanding[b] = false;
-  };
-
-  auto flush = [&]() {
-    wait_buf(0);              // every MMA of the window has completed
-    wait_buf(1);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    for (int c0 = 0; owner && c0 < n_real; c0 += 16) {
-      long long hi[16], lo[16];
+  if (warp == 0) {
+    // ------------------------------------------------ MMA issuer (one thread)
+    if (lane == 0) {
+      int g = 0, w = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+        const int2 U = units[u];
+        const GTask t = tasks[U.x];
+        const int nr = min(OZ_RC, t.m - U.y * OZ_RC);
+        const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
+        bool open = false;
+        int win = 0, cur = -1;
+        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+          const GItem I = items[it];
+          const int nst = oz_nst(I);
+          const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
+          for (int st = 0; st < nst && !stop; ++st) {
+            const bool start = !open || xb != cur || win + OZ_KC > OZ_WIN;
+            if (start) {
+              if (open) {           // the previous window of this unit is complete
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                    :: "r"(b_tfull));
+                ++w;
+              }
+              // the epilogue has read the previous window out of tensor memory
+              if (w > 0 && !oz_wait(b_tempty, (uint32_t)((w - 1) & 1), spin_limit, abortp, err)) {
+                stop = true;
+                break;
+              }
+              open = true;
+              win = 0;
+              cur = xb;
+            }
+            const int b = g & (OZ_RING - 1);
+            if (!oz_wait(b_full + 8u * b, (uint32_t)((g / OZ_RING) & 1), spin_limit, abortp, err)) {
+              stop = true;
+              break;
+            }
+            consumed_s = g + 1;
+            if (!oz_wait(b_digs + 8u * b, (uint32_t)((g / OZ_RING) & 1), spin_limit, abortp, err)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char* sA = smem + b * OZ_STAGE;
+            unsigned char* sB = sA + OZ_NS * OZ_A_BYTES;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
+            for (int p = 0; p < OZ_NS; ++p) {
+              const uint64_t da = sdesc(smem_u32(sA + p * OZ_A_BYTES), OZ_GROUP, 128);
 #pragma unroll
-      for (int L = 0; L < OZ_LV; ++L) {
-        uint32_t v[16];
-        uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(L * OZ_N + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          long long iv = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact integer
-          if (L < 4)
-            hi[j] += iv << (7 * (3 - L));
-          else
-            lo[j] += iv << (7 * (7 - L));
+              for (int q = 0; p + q < OZ_LV; ++q) {
+                const uint64_t db = sdesc(smem_u32(sB + q * OZ_B_BYTES), 128, (OZ_KR / 8) * 128);
+                // the first product of a level in a window overwrites it
+                // (every level is first reached in the p = 0 row)
+                const uint32_t accf = (start && p == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n"
+                    :: "r"(tmem + (uint32_t)((p + q) * OZ_N)), "l"(da), "l"(db), "r"(idesc),
+                       "r"(accf));
+              }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                :: "r"(b_empty + 8u * b));
+            ++g;
+            win += OZ_KC;
+          }
+        }
+        if (open && !stop) {
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+              :: "r"(b_tfull));
+          ++w;
         }
       }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int c = c0 + j;
-        const int sc = rexp[c >> 1] + F - 14;
-        acc[c] += ldexp((double)hi[j], sc - 19) + ldexp((double)lo[j], sc - 47);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ digit-panel copies
+    int g = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+      const GTask t = tasks[units[u].x];
+      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        const GItem I = items[it];
+        const int nst = oz_nst(I);
+        const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
+        const long long j00 = (long long)((I.in_row - (I.in_row & 3)) >> 2);
+        for (int st = 0; st < nst; ++st) {
+          const int b = g & (OZ_RING - 1);
+          // lane 0 waits for the stage buffer; the warp follows its verdict
+          bool okw = true;
+          if (lane == 0 && g >= OZ_RING)
+            okw = oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
+                          abortp, err);
+          if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) {
+            stop = true;
+            break;
+          }
+          const uint32_t fb = b_full + 8u * b;
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(fb), "r"(OZ_NS * OZ_A_BYTES) : "memory");
+          __syncwarp();
+          if (lane < OZ_NS) {
+            const long long j0 = j00 + 2LL * st;
+            const unsigned char* src = xp.xd[xb] + xd_off(lane, Y, y, xp.J[xb], j0, 0, 0);
+            const uint32_t dst = smem_u32(smem + b * OZ_STAGE + lane * OZ_A_BYTES);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                :: "r"(dst), "l"(src), "r"(OZ_A_BYTES), "r"(fb) : "memory");
+          }
+          ++g;
+          if (lane == 0) armed_s = g;
+        }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    ok = !__syncthreads_or(fail);   // TMEM reads done before the next window overwrites
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    fresh = true;
-    pending = false;
-    win = 0;
-  };
-
-  // matrix values of stage st of item it (this thread's two elements)
-  auto load_b = [&](int it, int st, double2* bv) {
-    const GItem I = items[it];
-    const double2* A = (const double2*)ab.p[I.a_buf] + I.a_off;
-    const int dl = I.in_row & 3;
+  } else if (warp < 4) {
+    // ------------------------------------------------ matrix digits (64 threads)
+    const int t2 = tid - 64;
+    int g = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+      const int2 U = units[u];
+      const GTask t = tasks[U.x];
+      const int rp = U.y * OZ_RC;
+      const int nr = min(OZ_RC, t.m - rp);
+      const int* rexp = task_row_exp + task_exp_off[U.x] + rp;
+      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        const GItem I = items[it];
+        const int nst = oz_nst(I);
+        const int dl = I.in_row & 3;
+        const double2* A = (const double2*)ab.p[I.a_buf] + I.a_off;
+        for (int st = 0; st < nst; ++st) {
+          // loads first (they do not need the stage buffer)
+          constexpr int EQ = OZ_RC * OZ_KC / OZ_BPROD;     // 4 elements per thread
+          double2 av[EQ];
+          int ex[EQ];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = tid + q * OZ_THREADS;
-      const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
-      const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
-      const int kr = st * OZ_KC + kk - dl;                // inner row within the item
-      bv[q] = make_double2(0.0, 0.0);
-      if (i < nr && kr >= 0 && kr < I.k)
-        bv[q] = I.trans ? A[(long long)kr * I.lda + rp + i] : A[(long long)(rp + i) * I.lda + kr];
-    }
-  };
-
-  int it = t.it0, st = 0;
-  double2 bv[2];
-  if (it < t.it1) load_b(it, 0, bv);
-  while (it < t.it1 && ok) {
-    const GItem I = items[it];
-    const int dl = I.in_row & 3;
-    const int nst = (I.k + dl + OZ_KC - 1) / OZ_KC;
-    const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
-    if (xb != cur_buf) {
-      if (pending) flush();
-      if (!ok) break;
-      cur_buf = xb;
-      const int* fe = xb ? fexp_far : fexp_in;
-      F = (col < nrhs) ? fe[col] : 0;
-    }
-    if (pending && win + OZ_KC > OZ_WIN) {
-      flush();
-      if (!ok) break;
-    }
-    const int sb = sidx & 1;
-    wait_buf(sb);             // the stage buffer is free once its previous MMAs committed
-    unsigned char* sA = smem + sb * OZ_STAGE;                  // digit planes of X'
-    unsigned char* sB = sA + OZ_NS * OZ_A_BYTES;               // digit planes of B'
-    // ---- X' digits: bulk copies of the pre-sliced panel (warp 1)
-    if (warp == 1) {
-      const uint32_t fb = bar_full + 8u * sb;
-      if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(fb), "r"(OZ_COPIES * OZ_COPY) : "memory");
-      __syncwarp();
-      const long long j0 = (long long)((I.in_row - dl) >> 2) + 4LL * st;
-      const unsigned char* base = xp.xd[xb];
-      for (int c = lane; c < OZ_COPIES; c += 32) {
-        const int p = c >> 4, gl = c & 15;
-        const unsigned char* src = base + xd_off(p, xp.G, (long long)blockIdx.y * 16 + gl,
-                                                 xp.J[xb], j0);
-        const uint32_t dst = smem_u32(sA + p * OZ_A_BYTES + gl * OZ_COPY);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-            :: "r"(dst), "l"(src), "r"(OZ_COPY), "r"(fb) : "memory");
-      }
-    }
-    landing[sb] = true;
-    // ---- B' digits of the prefetched matrix values, packed (re, im) pairs
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = tid + q * OZ_THREADS;
-      const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
-      const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
-      __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
-      digits(bv[q].x, rexp[i], ar);
-      digits(bv[q].y, rexp[i], ai);
-#pragma unroll
-      for (int s = 0; s < OZ_NS; ++s) {
-        unsigned char* bp = sB + s * OZ_B_BYTES;
-        *(uint32_t*)(bp + kmaj(2 * i, 2 * kk)) = pack2(ar[s], __hneg(ai[s]));
-        *(uint32_t*)(bp + kmaj(2 * i + 1, 2 * kk)) = pack2(ai[s], ar[s]);
-      }
-    }
-    // ---- next stage and its matrix loads (in flight during this stage's MMAs)
-    int it2 = it, st2 = st + 1;
-    if (st2 >= nst) {
-      it2 = it + 1;
-      st2 = 0;
-    }
-    if (it2 < t.it1) load_b(it2, st2, bv);
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    ok = !__syncthreads_or(fail);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) break;
-    if (tid == 0) {
-      if (!mbar_wait(bar_full + 8u * sb, ph_full[sb], spin_limit)) {
-        fail = true;
-        atomicExch(err, 1);
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int p = 0; p < OZ_NS; ++p)
-          for (int q = 0; p + q < OZ_LV; ++q) {
-            const int L = p + q;
-            for (int kh = 0; kh < OZ_KR / 16; ++kh) {
-              uint64_t da = sdesc(smem_u32(sA + p * OZ_A_BYTES) + kh * 256);
-              uint64_t db = sdesc(smem_u32(sB + q * OZ_B_BYTES) + kh * 256);
-              // the first product of a level in a window overwrites the level
-              // (levels are first reached in the p = 0 row of this loop)
-              uint32_t accf = (fresh && p == 0 && kh == 0) ? 0u : 1u;
-              asm volatile(
-                  "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n"
-                  :: "r"(tmem + (uint32_t)(L * OZ_N)), "l"(da), "l"(db), "r"(idesc), "r"(accf));
+          for (int q = 0; q < EQ; ++q) {
+            const int e = t2 + q * OZ_BPROD;
+            const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
+            const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
+            const int kr = st * OZ_KC + kk - dl;
+            av[q] = make_double2(0.0, 0.0);
+            ex[q] = 0;
+            if (i < nr && kr >= 0 && kr < I.k) {
+              av[q] = I.trans ? A[(long long)kr * I.lda + rp + i]
+                              : A[(long long)(rp + i) * I.lda + kr];
+              ex[q] = rexp[i];
             }
           }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-            :: "r"(bar_done + 8u * sb));
+          const int b = g & (OZ_RING - 1);
+          if (g >= OZ_RING &&
+              !oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
+                       abortp, err)) {
+            stop = true;
+            break;
+          }
+          unsigned char* sB = smem + b * OZ_STAGE + OZ_NS * OZ_A_BYTES;
+#pragma unroll
+          for (int q = 0; q < EQ; ++q) {
+            const int e = t2 + q * OZ_BPROD;
+            const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
+            const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
+            __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
+            digits(av[q].x, ex[q], ar);
+            digits(av[q].y, ex[q], ai);
+#pragma unroll
+            for (int s = 0; s < OZ_NS; ++s) {
+              unsigned char* bp = sB + s * OZ_B_BYTES;
+              *(uint32_t*)(bp + kmaj_b(2 * i, 2 * kk)) = pack2(ar[s], __hneg(ai[s]));
+              *(uint32_t*)(bp + kmaj_b(2 * i + 1, 2 * kk)) = pack2(ai[s], ar[s]);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;");
+          mbar_arrive(b_digs + 8u * b);
+          ++g;
+        }
       }
     }
-    ph_full[sb] ^= 1u;
-    landing[sb] = false;
-    outstanding[sb] = true;
-    ++sidx;
-    fresh = false;
-    pending = true;
-    win += OZ_KC;
-    it = it2;
-    st = st2;
-  }
-  if (ok && pending) flush();
-  wait_buf(0);                // nothing may still write tensor memory at release
-  wait_buf(1);
-  // copies issued but not consumed (a failed CTA): let them land (bounded)
-  if (tid == 0 || warp == 1) {
-    for (int b = 0; b < 2; ++b)
-      if (landing[b] && !mbar_wait(bar_full + 8u * b, ph_full[b], spin_limit) && tid == 0)
-        atomicExch(err, 1);
-  }
-  ok = !__syncthreads_or(fail);
-  if (ok && owner && col < nrhs) {
-    TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
-    const TY* base = (t.mode == 1) ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
-                                   : nullptr;
-    for (int i = 0; i < nr; ++i) {
-      double2 y = make_double2(acc[2 * i], acc[2 * i + 1]);
-      if (base) {
-        double2 b = to_d2(base[(long long)i * nrhs + col]);
-        y.x += b.x;
-        y.y += b.y;
+  } else {
+    // ------------------------------------------------ epilogue (warps 4-7)
+    const int row = tid - 128;                 // TMEM lane = RHS row of the tile
+    const int col = y * OZ_M + row;
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    int w = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+      const int2 U = units[u];
+      const GTask t = tasks[U.x];
+      const int rp = U.y * OZ_RC;
+      const int nr = min(OZ_RC, t.m - rp);
+      const int* rexp = task_row_exp + task_exp_off[U.x] + rp;
+      double acc[OZ_N];
+#pragma unroll
+      for (int c = 0; c < OZ_N; ++c) acc[c] = 0.0;
+      bool open = false;
+      int win = 0, cur = -1;
+      // read one completed window out of tensor memory into acc
+      auto drain = [&](int xb) {
+        // tcgen05.ld is warp-collective: the warp takes one verdict
+        const bool okw = oz_wait(b_tfull, (uint32_t)(w & 1), spin_limit, abortp, err);
+        if (!__all_sync(0xffffffffu, okw)) {
+          stop = true;
+          return;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int F = (col < nrhs) ? (xb ? fexp_far[col] : fexp_in[col]) : 0;
+#pragma unroll
+        for (int c0 = 0; c0 < OZ_N; c0 += 8) {
+          long long hi[8], lo[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            uint32_t v[4][8];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              const uint32_t ta = lane_base + (uint32_t)((4 * h + l) * OZ_N + c0);
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                  : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
+                    "=r"(v[l][5]), "=r"(v[l][6]), "=r"(v[l][7])
+                  : "r"(ta));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const long long iv = (long long)__float2int_rn(__uint_as_float(v[l][j]));
+                if (h == 0)
+                  hi[j] += iv << (7 * (3 - l));
+                else
+                  lo[j] += iv << (7 * (3 - l));
+              }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int sc = rexp[(c0 + j) >> 1 < nr ? (c0 + j) >> 1 : 0] + F - 14;
+            acc[c0 + j] += (double)hi[j] * pow2i(sc - 19) + (double)lo[j] * pow2i(sc - 47);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(b_tempty);
+        ++w;
+      };
+      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        const GItem I = items[it];
+        const int nst = oz_nst(I);
+        const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
+        for (int st = 0; st < nst && !stop; ++st) {
+          const bool start = !open || xb != cur || win + OZ_KC > OZ_WIN;
+          if (start) {
+            if (open) drain(cur);
+            open = true;
+            win = 0;
+            cur = xb;
+          }
+          win += OZ_KC;
+        }
       }
-      put(out + (long long)i * nrhs + col, y);
+      if (open && !stop) drain(cur);
+      if (stop || col >= nrhs) continue;
+      TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
+      const TY* base = (t.mode == 1)
+                           ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
+                           : nullptr;
+#pragma unroll
+      for (int i = 0; i < OZ_RC; ++i) {
+        if (i < nr) {
+          double2 yv = make_double2(acc[2 * i], acc[2 * i + 1]);
+          if (base) {
+            const double2 bv = to_d2(base[(long long)i * nrhs + col]);
+            yv.x += bv.x;
+            yv.y += bv.y;
+          }
+          put(out + (long long)i * nrhs + col, yv);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (abort_flag) {
+    // a CTA that gave up: its MMAs and copies complete before tensor memory
+    // and shared memory are released (bounded waits, abort flag ignored)
+    if (tid == 0) {
+      volatile int never = 0;
+      const long long lim = spin_limit > (1LL << 24) ? spin_limit : (1LL << 24);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+          :: "r"(b_fin));
+      oz_wait(b_fin, 0u, lim, &never, err);
+      for (int g = consumed_s; g < armed_s; ++g)
+        oz_wait(b_full + 8u * (g & (OZ_RING - 1)), (uint32_t)((g / OZ_RING) & 1), lim, &never,
+                err);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -469,12 +596,29 @@ __global__ void k_col_exp(const TV* __restrict__ V, int rows, int nrhs, int* out
 
 }  // namespace
 
-bool oz_ok_for(const TaskList& tl) { return !tl.tasks.empty(); }
-
-int oz_max_passes(const TaskList& tl) {
-  int mm = 1;
-  for (const GTask& t : tl.tasks) mm = std::max(mm, t.m);
-  return (mm + OZ_RC - 1) / OZ_RC;
+hm_status build_oz_units(TaskList& tl, size_t* dev_bytes) {
+  cudaFree(tl.d_units);
+  tl.d_units = nullptr;
+  tl.n_units = 0;
+  std::vector<std::pair<long long, int2>> u;
+  for (size_t q = 0; q < tl.tasks.size(); ++q) {
+    const GTask& t = tl.tasks[q];
+    long long cost = 2;                       // set-up and output rows of a unit
+    for (int it = t.it0; it < t.it1; ++it) cost += oz_nst(tl.items[it]);
+    for (int pass = 0; pass * OZ_RC < t.m; ++pass) u.push_back({cost, make_int2((int)q, pass)});
+  }
+  std::stable_sort(u.begin(), u.end(), [](const std::pair<long long, int2>& a,
+                                           const std::pair<long long, int2>& b) {
+    return a.first > b.first;
+  });
+  if (u.empty()) return HM_OK;
+  std::vector<int2> v(u.size());
+  for (size_t q = 0; q < u.size(); ++q) v[q] = u[q].second;
+  HM_CUDA(cudaMalloc((void**)&tl.d_units, v.size() * sizeof(int2)));
+  HM_CUDA(cudaMemcpy(tl.d_units, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  tl.n_units = (int)v.size();
+  if (dev_bytes) *dev_bytes += v.size() * sizeof(int2);
+  return HM_OK;
 }
 
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s) {
@@ -513,26 +657,32 @@ hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
                           cudaStream_t s, const int* row_exp, const long long* exp_off,
                           const int* fexp_in, const int* fexp_far, const OzPanels& xp,
                           long long spin_limit, int* err, bool panels32) {
-  if (tl.tasks.empty()) return HM_OK;
-  if (xp.G * 8 < nrhs) return HM_ERR_INVALID;
+  if (tl.tasks.empty() || tl.n_units == 0) return HM_OK;
+  if (xp.G * 8 < nrhs || xp.G % 16 != 0 || !tl.d_units) return HM_ERR_INVALID;
   static bool attr = false;
+  static int nsm = 0;
   if (!attr) {
     HM_CUDA(cudaFuncSetAttribute(k_oz_gather<double2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     HM_CUDA(cudaFuncSetAttribute(k_oz_gather<float2>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
-  dim3 grid((unsigned)tl.tasks.size(), (unsigned)((nrhs + OZ_M - 1) / OZ_M),
-            (unsigned)oz_max_passes(tl));
+  // one resident CTA per SM: the tiles of 128 RHS share the SMs
+  const int ytiles = (nrhs + OZ_M - 1) / OZ_M;
+  const int gx = std::max(1, std::min(tl.n_units, std::max(1, nsm / ytiles)));
+  dim3 grid((unsigned)gx, (unsigned)ytiles);
   if (panels32)
     k_oz_gather<float2><<<grid, OZ_THREADS, OZ_SMEM, s>>>(
-        tl.d_tasks, tl.d_items, vb, ab, nrhs, row_exp, exp_off, fexp_in, fexp_far, xp,
-        spin_limit, err);
+        tl.d_tasks, tl.d_items, tl.d_units, tl.n_units, vb, ab, nrhs, row_exp, exp_off, fexp_in,
+        fexp_far, xp, spin_limit, err);
   else
     k_oz_gather<double2><<<grid, OZ_THREADS, OZ_SMEM, s>>>(
-        tl.d_tasks, tl.d_items, vb, ab, nrhs, row_exp, exp_off, fexp_in, fexp_far, xp,
-        spin_limit, err);
+        tl.d_tasks, tl.d_items, tl.d_units, tl.n_units, vb, ab, nrhs, row_exp, exp_off, fexp_in,
+        fexp_far, xp, spin_limit, err);
   HM_CUDA(cudaGetLastError());
   return HM_OK;
 }
