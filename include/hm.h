@@ -171,7 +171,9 @@ hm_status hm_get_diagnostics(hm_handle h, double* ratio_host, double* resid_host
 /* Counts, as long long, in this order (up to n of them): N, leaves, near
  * blocks (upper), far blocks (upper), alpha entries, D entries, near entries
  * (upper), far factor entries, max rank, forward levels, backward levels,
- * device bytes held. */
+ * device bytes held, and the number of kernels the library has launched in
+ * this process so far (all handles; read it before and after a region to
+ * count that region's launches). */
 hm_status hm_get_stats(hm_handle h, long long* out_host, int n);
 
 /* Copy the leaf-order permutation (N int64, leaf position -> original index)

@@ -26,7 +26,8 @@ HM_ORDER_DFS, HM_ORDER_ND = 0, 1
 HM_FILL_FULL, HM_FILL_NEAR = 0, 1
 OPS = {"RT": 0, "R": 1, "DINV": 2, "FAR": 3, "NEAR": 4, "Z": 5}
 STATS = ("N", "leaves", "near_blocks", "far_blocks", "alpha_entries", "d_entries",
-         "near_entries", "far_entries", "max_rank", "fwd_levels", "bwd_levels", "device_bytes")
+         "near_entries", "far_entries", "max_rank", "fwd_levels", "bwd_levels", "device_bytes",
+         "kernel_launches")
 
 # every symbol include/hm.h declares
 SYMBOLS = ("hm_default_params", "hm_build", "hm_import", "hm_save", "hm_compute_scaling",

@@ -1,3 +1,4 @@
+#include <atomic>
 // C ABI of include/hm.h: handle life cycle, block-file import/export, the
 // level schedules of the sweeps, and the power-series solve chain.
 //
@@ -18,6 +19,10 @@
 using namespace hm;
 
 namespace hm {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 hm_status cuda_status(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return HM_ERR_OOM;
@@ -77,6 +82,8 @@ void free_tasks(TaskList& tl) {
   cudaFree(tl.d_tiles);
   cudaFree(tl.d_toff);
   cudaFree(tl.d_units);
+  cudaFree(tl.d_torder);
+  tl.d_torder = nullptr;
   tl.d_units = nullptr;
   tl.n_units = 0;
   tl.d_tasks = nullptr;
@@ -417,6 +424,10 @@ hm_status build_schedules(hm_ctx* h) {
   }
   for (int l = 0; l < n; ++l) {
     GTask t{VB_OUT, (int)h->leaf_off[l], h->m[l], (int)h->far2_tl.items.size(), 0, 0, 0, 0};
+    // stage-1 panel items first, then the dense blocks on the input: the
+    // FP64-accurate engine changes its input scale at most once per task
+    std::stable_partition(per_leaf[l].begin(), per_leaf[l].end(),
+                          [](const GItem& it) { return it.in_buf == VB_FAR; });
     for (auto& it : per_leaf[l]) {
       h->far2_tl.items.push_back(it);
       h->far2_tl.flops += (long long)h->m[l] * it.k;
@@ -1119,10 +1130,10 @@ hm_status hm_get_stats(hm_handle h, long long* out, int n) {
   for (int k = 0; k < (int)h->rows.size(); ++k)
     for (int j : h->rows[k]) a_e += (long long)h->m[h->elim[k]] * h->m[h->elim[j]];
   for (int k = 0; k < h->nl; ++k) d_e += (long long)h->m[k] * h->m[k];
-  long long v[12] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
+  long long v[13] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
                      near_e, far_e, maxr, (long long)h->fwd.part.size(),
-                     (long long)h->bwd.part.size(), (long long)h->dev_bytes};
-  for (int i = 0; i < n && i < 12; ++i) out[i] = v[i];
+                     (long long)h->bwd.part.size(), (long long)h->dev_bytes, hm::launch_count()};
+  for (int i = 0; i < n && i < 13; ++i) out[i] = v[i];
   return HM_OK;
 }
 

@@ -60,6 +60,7 @@ struct TaskList {
   // into bf16 tiles (hm_tc.cu), task t's tiles from byte d_toff[t]
   unsigned char* d_tiles = nullptr;
   long long* d_toff = nullptr;
+  int* d_torder = nullptr;   // task order of the persistent kernel, costliest first
   size_t tile_bytes = 0;
   // FP64-accurate path: work units (task, 32-row pass), costliest first
   int2* d_units = nullptr;
@@ -227,8 +228,16 @@ hm_status launch_plane_wave(const double* d_verts, const int* d_tris, const int*
 hm_status cuda_status(cudaError_t e);
 int prof_begin(hm_ctx* h);                                   // -1 when disabled
 void prof_end(hm_ctx* h, int ev, int cat, double bytes, double flops);
+// kernels launched by the library in this process (hm_get_stats)
+void note_launch();
+long long launch_count();
 }  // namespace hm
 
+#define HM_LAUNCHED()              \
+  do {                             \
+    hm::note_launch();             \
+    HM_CUDA(cudaGetLastError());   \
+  } while (0)
 #define HM_CUDA(x)                                       \
   do {                                                   \
     cudaError_t _e = (x);                                \

@@ -415,7 +415,7 @@ hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int
     launch_tl<float2, float2, float2>(tl, vb, ab, nrhs, s);
   else
     launch_tl<double2, float2, double2>(tl, vb, ab, nrhs, s);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
@@ -435,67 +435,67 @@ hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t 
   else
     k_finalize<float2><<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots,
                                                                            vb, nrhs);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_gather_perm32(const cplx* B, float2* V, const int* perm, int N, int nrhs,
                                cudaStream_t s) {
   k_gather_perm32<<<grid_for((long long)N * nrhs), 256, 0, s>>>(B, V, perm, N, nrhs);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_to32(const cplx* a, float2* o, size_t n, cudaStream_t s) {
   k_to32<<<grid_for((long long)n), 256, 0, s>>>(a, o, n);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_axpby64_32(cplx* o, double sa, const float2* b, double sb, size_t n,
                             cudaStream_t s) {
   k_axpby64_32<<<grid_for((long long)n), 256, 0, s>>>(o, sa, b, sb, n);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_axpby32(float2* out, const float2* a, float sa, const float2* b, float sb,
                          size_t n, cudaStream_t s) {
   k_axpby32<<<grid_for((long long)n), 256, 0, s>>>(out, a, sa, b, sb, n);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_col_norms2_32(const float2* V, int N, int nrhs, double* out, cudaStream_t s) {
   k_col_norms2_32<<<nrhs, 256, 0, s>>>(V, N, nrhs, out);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s) {
   k_gather_perm<<<grid_for((long long)N * nrhs), 256, 0, s>>>(B, V, perm, N, nrhs);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,
                               cudaStream_t s) {
   k_scatter_perm<<<grid_for((long long)N * nrhs), 256, 0, s>>>(V, X, perm, N, nrhs);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_axpby(cplx* out, const cplx* a, double sa, const cplx* b, double sb, size_t n,
                        cudaStream_t s) {
   k_axpby<<<grid_for((long long)n), 256, 0, s>>>(out, a, sa, b, sb, n);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_col_norms2(const cplx* V, int N, int nrhs, double* out, cudaStream_t s) {
   k_col_norms2<<<nrhs, 256, 0, s>>>(V, N, nrhs, out);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 

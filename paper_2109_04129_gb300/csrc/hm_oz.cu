@@ -17,10 +17,13 @@
 //     (256 complex rows) every partial sum is an integer of magnitude <= 2^24
 //     and the FP32 accumulation is exact;
 //   * after each window the levels are combined exactly in int64 (levels 0-3
-//     and 4-7 in two words) and added to FP64 accumulators with the factor
-//     2^(E_i + F_r - 110 + 7 (14 - L)).
+//     and 4-7 in two words, weights 2^(E_i + F_r - 110 + 7 (14 - L))), the two
+//     words into one (bits below 2^-49 of the row and column scales dropped),
+//     and that word is added to an FP64 accumulator with one fused
+//     multiply-add.
 // Dropped terms (L >= 8) and the truncated bits are below 2^-55 of the
-// row/column scales times the inner length: FP64-class accuracy.
+// row/column scales times the inner length, plus 2^-49 of the scales per
+// window: FP64-class accuracy.
 //
 // Complex products use the real-expanded block (rows [a_re, -a_im] and
 // [a_im, a_re] over interleaved inner k) as in the mixed-precision engine.
@@ -39,7 +42,10 @@
 // unit is (task, 32-row pass); each CTA walks its share of the units,
 // costliest first, for one tile of 128 right-hand sides.  Warp 1 issues the
 // bulk copies, warps 2-3 slice the matrix digits, warp 0 (one thread) issues
-// the 36 MMAs of a stage, warps 4-7 read the level accumulators out of tensor
+// the MMAs of a stage (the matrix digit planes are stacked along N and the
+// levels spaced by the same width, so one MMA per input plane adds all of its
+// digit products into their levels: 8 to 12 MMAs for the 36 products), warps
+// 4-7 read the level accumulators out of tensor
 // memory and keep the FP64 sums.  They hand over through mbarriers: a ring of
 // four shared-memory stages (full: copies landed; digits: matrix digits
 // written; empty: the MMAs that read it completed) and the tensor-memory
@@ -50,6 +56,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "hm_internal.h"
@@ -81,6 +88,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // B' (matrix) tile: canonical K-major, 8-row groups of (OZ_KR / 8) core matrices
 __device__ __forceinline__ uint32_t kmaj_b(int row, int k) {
   return ((row >> 3) * (OZ_KR >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+// element (i, kk) of the 32 x 8 matrix tile handled by producer slot e: a
+// warp's 32 lanes cover 4 rows x 8 inner rows, so both the global loads
+// (4 consecutive rows, or 8 consecutive inner rows) and the shared stores
+// stay compact
+__device__ __forceinline__ void oz_elem(int e, int trans, int& i, int& kk) {
+  const int lane = e & 31, grp = e >> 5;
+  if (trans) {
+    i = 4 * grp + (lane & 3);
+    kk = lane >> 2;
+  } else {
+    i = 4 * grp + (lane >> 3);
+    kk = lane & 7;
+  }
 }
 // shared-memory matrix descriptor (no swizzle): lbo = byte distance of
 // K-adjacent core matrices, sbo = byte distance of adjacent 8-row groups
@@ -116,7 +137,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // Eight balanced base-128 digits of trunc(v 2^(55 - S)) for |v| < 2^S
 // (integer operations only): d_1..d_7 in [-64, 63], d_0 in [0, 64], then the
-// sign of v.
+// sign of v.  Adding 64 to each of the seven low base-128 positions turns the
+// balanced digits into plain 7-bit fields (the additions carry exactly as the
+// balanced representation needs): d_p = field_p - 64, d_0 = the bits above.
+constexpr unsigned long long OZ_BIAS = 0x1020408102040ull;   // sum of 64 * 128^m, m = 0..6
 __device__ __forceinline__ void digits(double v, int S, __nv_bfloat16* d) {
   unsigned long long b = (unsigned long long)__double_as_longlong(v);
   int e = (int)((b >> 52) & 0x7FF);
@@ -129,18 +153,12 @@ __device__ __forceinline__ void digits(double v, int S, __nv_bfloat16* d) {
     else
       U = (-sh < 64) ? (M >> (-sh)) : 0ull;
   }
-  const bool neg = (b >> 63) != 0;
-  int carry = 0;
+  const unsigned long long V = U + OZ_BIAS;
+  const int sg = (b >> 63) ? -1 : 1;
+  d[0] = __int2bfloat16_rn(sg * (int)(V >> 49));
 #pragma unroll
-  for (int p = OZ_NS - 1; p >= 0; --p) {
-    int s = (int)((U >> (49 - 7 * p)) & 0x7F) + carry;
-    carry = 0;
-    if (p > 0 && s >= 64) {
-      s -= 128;
-      carry = 1;
-    }
-    d[p] = __int2bfloat16_rn(neg ? -s : s);
-  }
+  for (int p = 1; p < OZ_NS; ++p)
+    d[p] = __int2bfloat16_rn(sg * ((int)((V >> (49 - 7 * p)) & 0x7F) - 64));
 }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
     long long spin_limit, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bars[3 * OZ_RING + 3];
+  __shared__ __align__(8) uint64_t bars[3 * OZ_RING + 5];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int armed_s, consumed_s;     // stages armed by the copy warp / taken by the MMA warp
@@ -227,8 +245,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
   const uint32_t b_digs = smem_u32(&bars[OZ_RING]);       // + 8 b: matrix digits of b written
   const uint32_t b_empty = smem_u32(&bars[2 * OZ_RING]);  // + 8 b: MMAs reading b completed
   const uint32_t b_tfull = smem_u32(&bars[3 * OZ_RING]);
-  const uint32_t b_tempty = b_tfull + 8;
-  const uint32_t b_fin = b_tfull + 16;
+  const uint32_t b_tempty = b_tfull + 16;                 // + 8 (w & 1)
+  const uint32_t b_fin = b_tfull + 32;
   volatile int* abortp = &abort_flag;
   const int y = blockIdx.y;
   const int Y = xp.G / 16;
@@ -239,8 +257,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
                    "r"(OZ_BPROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_empty + 8u * b));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tfull));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_tempty), "r"(OZ_M));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tfull + 8u * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_tempty + 8u * b), "r"(OZ_M));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_fin));
     abort_flag = 0;
     armed_s = 0;
@@ -259,18 +279,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
 
   if (warp == 0) {
     // ------------------------------------------------ MMA issuer (one thread)
+    // Tensor memory holds the 8 level accumulators of a window: a narrow unit
+    // (N = 32 columns per level) uses one half (window w in half w & 1, so the
+    // epilogue drains one window while the next one accumulates), a wide unit
+    // (N = 64) uses all 512 columns.  Before window w the columns it writes
+    // must have been drained: window w - 2 always, window w - 1 as well when
+    // either of the two is wide.  Window w completes tfull[w & 1]; its drain
+    // completes tempty[w & 1] (the waited window is always the latest one of
+    // its parity, so a parity wait cannot alias).
     if (lane == 0) {
       int g = 0, w = 0;
-      bool stop = false;
+      bool stop = false, prev_wide = false;
       for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
         const int2 U = units[u];
         const GTask t = tasks[U.x];
         const int nr = min(OZ_RC, t.m - U.y * OZ_RC);
         const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                               ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
+        const bool wide = n_real > 32;
+        // instruction descriptor without N (bf16 x bf16 -> f32, K-major, M = 128)
+        const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_M >> 4) << 24);
+        const int cmax = 256 / n_real;          // B' planes per MMA (N <= 256)
+        const uint32_t pb = (uint32_t)n_real * (OZ_KR * 2);   // bytes of one B' plane
         bool open = false;
         int win = 0, cur = -1;
+        uint32_t cbase = 0;
         for (int it = t.it0; it < t.it1 && !stop; ++it) {
           const GItem I = items[it];
           const int nst = oz_nst(I);
@@ -281,17 +313,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
               if (open) {           // the previous window of this unit is complete
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                    :: "r"(b_tfull));
+                    :: "r"(b_tfull + 8u * (w & 1)));
+                prev_wide = wide;
                 ++w;
               }
-              // the epilogue has read the previous window out of tensor memory
-              if (w > 0 && !oz_wait(b_tempty, (uint32_t)((w - 1) & 1), spin_limit, abortp, err)) {
+              const int need = (wide || prev_wide) ? w - 1 : w - 2;   // drained before window w
+              if (need >= 0 && !oz_wait(b_tempty + 8u * (need & 1), (uint32_t)((need >> 1) & 1),
+                                        spin_limit, abortp, err)) {
                 stop = true;
                 break;
               }
               open = true;
               win = 0;
               cur = xb;
+              cbase = wide ? 0u : (uint32_t)(w & 1) * 256u;
             }
             const int b = g & (OZ_RING - 1);
             if (!oz_wait(b_full + 8u * b, (uint32_t)((g / OZ_RING) & 1), spin_limit, abortp, err)) {
@@ -305,21 +340,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char* sA = smem + b * OZ_STAGE;
-            unsigned char* sB = sA + OZ_NS * OZ_A_BYTES;
+            // descriptors of plane 0; plane p is p * plane-bytes / 16 further in the
+            // address field (all shared addresses stay below 256 KB: no carry)
+            const uint64_t da0 = sdesc(smem_u32(sA), OZ_GROUP, 128);
+            const uint64_t db0 = sdesc(smem_u32(sA + OZ_NS * OZ_A_BYTES), 128, (OZ_KR / 8) * 128);
+            const uint32_t acc0 = start ? 0u : 1u;
+            // The B' planes q = 0..7 are stacked along N and level L sits at
+            // columns L * n_real, so one MMA of A' plane p against planes
+            // q0 .. q0 + cnt - 1 (N = cnt * n_real) adds each product d_p d_q
+            // into its level p + q: 8 to 12 MMAs per stage instead of 36.
 #pragma unroll
             for (int p = 0; p < OZ_NS; ++p) {
-              const uint64_t da = sdesc(smem_u32(sA + p * OZ_A_BYTES), OZ_GROUP, 128);
-#pragma unroll
-              for (int q = 0; p + q < OZ_LV; ++q) {
-                const uint64_t db = sdesc(smem_u32(sB + q * OZ_B_BYTES), 128, (OZ_KR / 8) * 128);
-                // the first product of a level in a window overwrites it
-                // (every level is first reached in the p = 0 row)
-                const uint32_t accf = (start && p == 0) ? 0u : 1u;
+              const uint64_t da = da0 + (uint64_t)(p * (OZ_A_BYTES >> 4));
+              // every level is first reached by the p = 0 MMAs: they overwrite
+              const uint32_t accf = p == 0 ? acc0 : 1u;
+              for (int q0 = 0; q0 < OZ_LV - p; q0 += cmax) {
+                const int cnt = min(cmax, OZ_LV - p - q0);
+                const uint32_t idesc = idesc0 | ((uint32_t)((cnt * n_real) >> 3) << 17);
+                const uint64_t db = db0 + (uint64_t)((q0 * pb) >> 4);
                 asm volatile(
                     "{\n .reg .pred pp;\n setp.ne.b32 pp, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}\n"
-                    :: "r"(tmem + (uint32_t)((p + q) * OZ_N)), "l"(da), "l"(db), "r"(idesc),
-                       "r"(accf));
+                    :: "r"(tmem + cbase + (uint32_t)((p + q0) * n_real)), "l"(da), "l"(db),
+                       "r"(idesc), "r"(accf));
               }
             }
             asm volatile(
@@ -332,7 +375,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         if (open && !stop) {
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-              :: "r"(b_tfull));
+              :: "r"(b_tfull + 8u * (w & 1)));
+          prev_wide = wide;
           ++w;
         }
       }
@@ -388,57 +432,86 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       const int rp = U.y * OZ_RC;
       const int nr = min(OZ_RC, t.m - rp);
       const int* rexp = task_row_exp + task_exp_off[U.x] + rp;
-      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+      // the unit's B' planes are n_real rows each, stacked back to back
+      const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
+      const int ne = (n_real / 2) * OZ_KC;                 // elements of one plane
+      const uint32_t pb = (uint32_t)n_real * (OZ_KR * 2);  // bytes of one plane
+      constexpr int EQ = OZ_RC * OZ_KC / OZ_BPROD;       // up to 4 elements per thread
+      // matrix values (and row exponents) of stage st of item it
+      auto load = [&](int it, int st, double2* av, int* ex) {
         const GItem I = items[it];
-        const int nst = oz_nst(I);
-        const int dl = I.in_row & 3;
         const double2* A = (const double2*)ab.p[I.a_buf] + I.a_off;
-        for (int st = 0; st < nst; ++st) {
-          // loads first (they do not need the stage buffer)
-          constexpr int EQ = OZ_RC * OZ_KC / OZ_BPROD;     // 4 elements per thread
-          double2 av[EQ];
-          int ex[EQ];
+        const int dl = I.in_row & 3;
 #pragma unroll
-          for (int q = 0; q < EQ; ++q) {
-            const int e = t2 + q * OZ_BPROD;
-            const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
-            const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
-            const int kr = st * OZ_KC + kk - dl;
-            av[q] = make_double2(0.0, 0.0);
-            ex[q] = 0;
-            if (i < nr && kr >= 0 && kr < I.k) {
-              av[q] = I.trans ? A[(long long)kr * I.lda + rp + i]
-                              : A[(long long)(rp + i) * I.lda + kr];
-              ex[q] = rexp[i];
-            }
+        for (int q = 0; q < EQ; ++q) {
+          int i, kk;
+          oz_elem(t2 + q * OZ_BPROD, I.trans, i, kk);
+          const int kr = st * OZ_KC + kk - dl;
+          av[q] = make_double2(0.0, 0.0);
+          ex[q] = 0;
+          if (t2 + q * OZ_BPROD < ne && i < nr && kr >= 0 && kr < I.k) {
+            av[q] = I.trans ? A[(long long)kr * I.lda + rp + i] : A[(long long)(rp + i) * I.lda + kr];
+            ex[q] = rexp[i];
           }
-          const int b = g & (OZ_RING - 1);
-          if (g >= OZ_RING &&
-              !oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
-                       abortp, err)) {
-            stop = true;
-            break;
-          }
-          unsigned char* sB = smem + b * OZ_STAGE + OZ_NS * OZ_A_BYTES;
-#pragma unroll
-          for (int q = 0; q < EQ; ++q) {
-            const int e = t2 + q * OZ_BPROD;
-            const int i = I.trans ? (e % OZ_RC) : (e / OZ_KC);
-            const int kk = I.trans ? (e / OZ_RC) : (e % OZ_KC);
-            __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
-            digits(av[q].x, ex[q], ar);
-            digits(av[q].y, ex[q], ai);
-#pragma unroll
-            for (int s = 0; s < OZ_NS; ++s) {
-              unsigned char* bp = sB + s * OZ_B_BYTES;
-              *(uint32_t*)(bp + kmaj_b(2 * i, 2 * kk)) = pack2(ar[s], __hneg(ai[s]));
-              *(uint32_t*)(bp + kmaj_b(2 * i + 1, 2 * kk)) = pack2(ai[s], ar[s]);
-            }
-          }
-          asm volatile("fence.proxy.async.shared::cta;");
-          mbar_arrive(b_digs + 8u * b);
-          ++g;
         }
+      };
+      // the unit's stages in order (items without stages skipped); the loads
+      // of the next stage are in flight while this one is sliced
+      int it = t.it0, st = 0;
+      while (it < t.it1 && oz_nst(items[it]) == 0) ++it;
+      double2 av[EQ], avn[EQ];
+      int ex[EQ], exn[EQ];
+      if (it < t.it1) load(it, 0, av, ex);
+      while (it < t.it1 && !stop) {
+        const int trans = items[it].trans;
+        int it2 = it, st2 = st + 1;
+        if (st2 >= oz_nst(items[it])) {
+          st2 = 0;
+          ++it2;
+          while (it2 < t.it1 && oz_nst(items[it2]) == 0) ++it2;
+        }
+        if (it2 < t.it1) load(it2, st2, avn, exn);
+        const int b = g & (OZ_RING - 1);
+        if (g >= OZ_RING &&
+            !oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
+                     abortp, err)) {
+          stop = true;
+          break;
+        }
+        unsigned char* sB = smem + b * OZ_STAGE + OZ_NS * OZ_A_BYTES;
+#pragma unroll
+        for (int q = 0; q < EQ; ++q) {
+          if (t2 + q * OZ_BPROD >= ne) continue;
+          int i, kk;
+          oz_elem(t2 + q * OZ_BPROD, trans, i, kk);
+          __nv_bfloat16 ar[OZ_NS], ai[OZ_NS];
+          digits(av[q].x, ex[q], ar);
+          digits(av[q].y, ex[q], ai);
+          // rows 2i and 2i+1 sit 16 bytes apart: lanes with kk >= 4 store
+          // them in the other order, so each store instruction of the warp
+          // hits 32 distinct banks
+          const bool sw = (kk & 4) != 0;
+          const uint32_t o0 = kmaj_b(2 * i + (sw ? 1 : 0), 2 * kk);
+          const uint32_t o1 = kmaj_b(2 * i + (sw ? 0 : 1), 2 * kk);
+#pragma unroll
+          for (int s = 0; s < OZ_NS; ++s) {
+            unsigned char* bp = sB + s * pb;
+            const uint32_t w_re = pack2(ar[s], __hneg(ai[s]));   // row 2i:   [a_re, -a_im]
+            const uint32_t w_im = pack2(ai[s], ar[s]);           // row 2i+1: [a_im,  a_re]
+            *(uint32_t*)(bp + o0) = sw ? w_im : w_re;
+            *(uint32_t*)(bp + o1) = sw ? w_re : w_im;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        mbar_arrive(b_digs + 8u * b);
+        ++g;
+#pragma unroll
+        for (int q = 0; q < EQ; ++q) {
+          av[q] = avn[q];
+          ex[q] = exn[q];
+        }
+        it = it2;
+        st = st2;
       }
     }
   } else {
@@ -459,18 +532,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       for (int c = 0; c < OZ_N; ++c) acc[c] = 0.0;
       bool open = false;
       int win = 0, cur = -1;
-      // read one completed window out of tensor memory into acc
-      auto drain = [&](int xb) {
+      // read one completed window out of tensor memory into acc (NC columns
+      // per level, level stride NC)
+      auto drain_nc = [&](auto ncc, int xb) {
+        constexpr int NC = decltype(ncc)::value;
         // tcgen05.ld is warp-collective: the warp takes one verdict
-        const bool okw = oz_wait(b_tfull, (uint32_t)(w & 1), spin_limit, abortp, err);
+        const bool okw = oz_wait(b_tfull + 8u * (w & 1), (uint32_t)((w >> 1) & 1), spin_limit,
+                                 abortp, err);
         if (!__all_sync(0xffffffffu, okw)) {
           stop = true;
           return;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int F = (col < nrhs) ? (xb ? fexp_far[col] : fexp_in[col]) : 0;
+        // a narrow window lives in tensor-memory half w & 1, a wide one in all
+        const uint32_t cb = (NC == 32) ? (uint32_t)(w & 1) * 256u : 0u;
 #pragma unroll
-        for (int c0 = 0; c0 < OZ_N; c0 += 8) {
+        for (int c0 = 0; c0 < NC; c0 += 8) {
+          int rx[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) rx[r] = rexp[(c0 / 2 + r) < nr ? (c0 / 2 + r) : 0];
           long long hi[8], lo[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
@@ -479,7 +560,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
             uint32_t v[4][8];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-              const uint32_t ta = lane_base + (uint32_t)((4 * h + l) * OZ_N + c0);
+              const uint32_t ta = lane_base + cb + (uint32_t)((4 * h + l) * NC + c0);
               asm volatile(
                   "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                   : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]),
@@ -498,15 +579,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
                   lo[j] += iv << (7 * (3 - l));
               }
           }
+          // one word hi 2^16 + lo / 2^12 (|hi|, |lo| < 2^45.1: no overflow; the
+          // dropped bits are below 2^-49 of the row and column scales), in
+          // units of 2^(E_i + F_r - 49), then one fused multiply-add
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int sc = rexp[(c0 + j) >> 1 < nr ? (c0 + j) >> 1 : 0] + F - 14;
-            acc[c0 + j] += (double)hi[j] * pow2i(sc - 19) + (double)lo[j] * pow2i(sc - 47);
+            const long long V = (hi[j] << 16) + (lo[j] >> 12);
+            const int sc = rx[j >> 1] + F - 14;
+            acc[c0 + j] = fma((double)V, pow2i(sc - 35), acc[c0 + j]);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        mbar_arrive(b_tempty);
+        mbar_arrive(b_tempty + 8u * (w & 1));
         ++w;
+      };
+      // level L of the unit sits at columns L * n_real (n_real = 32, 48 or 64)
+      const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
+      auto drain = [&](int xb) {
+        if (n_real == 32)
+          drain_nc(std::integral_constant<int, 32>{}, xb);
+        else if (n_real == 48)
+          drain_nc(std::integral_constant<int, 48>{}, xb);
+        else
+          drain_nc(std::integral_constant<int, 64>{}, xb);
       };
       for (int it = t.it0; it < t.it1 && !stop; ++it) {
         const GItem I = items[it];
@@ -623,13 +718,13 @@ hm_status build_oz_units(TaskList& tl, size_t* dev_bytes) {
 
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s) {
   k_col_exp<double2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_col_exp32(const float2* V, int rows, int nrhs, int* out, cudaStream_t s) {
   k_col_exp<float2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
@@ -649,7 +744,7 @@ hm_status launch_digitize(const void* V, bool f32, int rows, int nrhs, const int
     k_digitize<float2><<<blocks, 256, 0, s>>>((const float2*)V, rows, nrhs, fexp, out, J, G);
   else
     k_digitize<double2><<<blocks, 256, 0, s>>>((const double2*)V, rows, nrhs, fexp, out, J, G);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 
@@ -683,7 +778,7 @@ hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
     k_oz_gather<double2><<<grid, OZ_THREADS, OZ_SMEM, s>>>(
         tl.d_tasks, tl.d_items, tl.d_units, tl.n_units, vb, ab, nrhs, row_exp, exp_off, fexp_in,
         fexp_far, xp, spin_limit, err);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   return HM_OK;
 }
 

@@ -408,7 +408,7 @@ hm_status hm_compute_scaling(hm_handle h) {
         HM_CUDA(cudaMalloc((void**)&dC, lst->size() * sizeof(CopyJob)));
         HM_CUDA(cudaMemcpy(dC, lst->data(), lst->size() * sizeof(CopyJob), cudaMemcpyHostToDevice));
         k_copy_blocks<<<(unsigned)lst->size(), 256>>>(dC, h->d_near, lst == &jd ? dZd : dZ);
-        HM_CUDA(cudaGetLastError());
+        HM_LAUNCHED();
         HM_CUDA(cudaDeviceSynchronize());
         cudaFree(dC);
         dC = nullptr;
@@ -464,7 +464,7 @@ hm_status hm_compute_scaling(hm_handle h) {
       auto ss = step_schur[k];
       if (ss.second > ss.first) k_bgemm<<<(unsigned)(ss.second - ss.first), 256>>>(dT + ss.first);
     }
-    HM_CUDA(cudaGetLastError());
+    HM_LAUNCHED();
     HM_CUDA(cudaDeviceSynchronize());
     int flag = 0;
     HM_CUDA(cudaMemcpy(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost));

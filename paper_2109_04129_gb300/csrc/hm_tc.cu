@@ -45,7 +45,6 @@ constexpr int TC_THREADS = 256;     // two halves share the staging; warps 0-3 o
 constexpr int A_SLICE_BYTES = TC_M * TC_KR * 2;       // 8 KB
 constexpr int B_SLICE_BYTES = TC_NMAX * TC_KR * 2;    // 16 KB
 constexpr int TC_STAGE = TC_NS * (A_SLICE_BYTES + B_SLICE_BYTES);   // 72 KB
-constexpr int TC_SMEM = 2 * TC_STAGE + 1024;                       // double buffered
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -75,18 +74,6 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16* s) {
   s[2] = __float2bfloat16_rn(r2);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit) {
-  uint32_t done = 0;
-  for (long long it = 0; it < limit; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase));
-    if (done) return true;
-  }
-  return false;
-}
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -137,212 +124,352 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
   }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gather(
-    const GTask* __restrict__ tasks, const GItem* __restrict__ items, VBufs vb,
+constexpr int TC_RING = 3;                 // shared-memory stages of the gather
+constexpr int TC_XPROD = 128;              // right-hand-side split threads (warps 2-5)
+constexpr int TC_WTHREADS = 320;           // 10 warps
+constexpr int TC_GSMEM = TC_RING * TC_STAGE + 1024;
+
+// bounded wait that also gives up when another role has aborted the CTA
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase, long long limit,
+                                        volatile int* abort_flag, int* err) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase));
+    if (done) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void tc_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(bar));
+}
+// the 16-row stages of an item
+__device__ __forceinline__ int tc_nst(const GItem& I) { return (I.k + TC_KC - 1) / TC_KC; }
+
+// Persistent, warp-specialised gather GEMM on complex64 lists.  Each CTA
+// walks its share of the tasks (costliest first) for one tile of 128 RHS:
+//   warp 0 (one thread) issues the 12 MMAs of a stage (6 slice products x 2 K
+//     steps) into the task's accumulator, tensor-memory half j & 1 for the
+//     CTA's j-th task, so the epilogue of one task overlaps the next task;
+//   warp 1 (one thread) fetches the stage's pre-split matrix tile (three bulk
+//     copies, completion on the stage's "tile" mbarrier);
+//   warps 2-5 split the stage's right-hand sides (thread = RHS row; loads of
+//     the next stage in flight while this one is split and stored);
+//   warps 6-9 read the accumulator (thread = TMEM lane = RHS row), add the
+//     base rows and store complex64 outputs.
+// Stage buffers form a ring of TC_RING: tile[b] + split[b] full -> MMAs ->
+// empty[b]; accumulators: tfull[h] (MMAs of a task done) -> epilogue ->
+// tempty[h].  Every wait is bounded and watches a CTA-wide abort flag.
+__global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
+    const GTask* __restrict__ tasks, const GItem* __restrict__ items,
+    const int* __restrict__ order, int n_tasks, VBufs vb,
     const unsigned char* __restrict__ tiles, const long long* __restrict__ toff, int nrhs,
     long long spin_limit, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t mbar[4];   // [b]: MMAs of buffer b done; [2 + b]: its tile landed
+  __shared__ __align__(8) uint64_t bars[3 * TC_RING + 5];
   __shared__ uint32_t tmem_base;
-  const GTask t = tasks[blockIdx.x];
-  if (t.m <= 0) return;                                      // whole CTA: uniform
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (TC_M - 1), half = tid >> 7;
-  const int r0 = blockIdx.y * TC_M;
-  const int col = r0 + row;
-  const int n_real = tc_nreal(t.m);                          // MMA N
-  const uint32_t ncols = n_real <= 32 ? 32 : (n_real <= 64 ? 64 : (n_real <= 128 ? 128 : 256));
-  const uint32_t plane = (uint32_t)n_real * 64;              // bytes of one slice plane of a tile
-  const uint32_t bar_done = smem_u32(&mbar[0]);
-  const uint32_t bar_full = smem_u32(&mbar[2]);
+  __shared__ int abort_flag;
+  __shared__ int armed_s, consumed_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t b_tile = __cvta_generic_to_shared(&bars[0]);               // + 8 b
+  const uint32_t b_split = __cvta_generic_to_shared(&bars[TC_RING]);        // + 8 b
+  const uint32_t b_empty = __cvta_generic_to_shared(&bars[2 * TC_RING]);    // + 8 b
+  const uint32_t b_tfull = __cvta_generic_to_shared(&bars[3 * TC_RING]);    // + 8 h
+  const uint32_t b_tempty = b_tfull + 16;                                    // + 8 h
+  const uint32_t b_fin = b_tfull + 32;
+  volatile int* abortp = &abort_flag;
+  const int y = blockIdx.y;
   if (tid == 0) {
-    for (int b = 0; b < 4; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_done + 8u * b));
+    for (int b = 0; b < TC_RING; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tile + 8u * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_split + 8u * b),
+                   "r"(TC_XPROD));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_empty + 8u * b));
+    }
+    for (int h = 0; h < 2; ++h) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tfull + 8u * h));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_tempty + 8u * h),
+                   "r"(TC_M));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_fin));
+    abort_flag = 0;
+    armed_s = 0;
+    consumed_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base)), "r"(ncols));
+                 :: "r"((uint32_t)__cvta_generic_to_shared(&tmem_base)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_real >> 3) << 17) |
-                         ((uint32_t)(TC_M >> 4) << 24);
-  uint32_t ph_done[2] = {0u, 0u}, ph_full[2] = {0u, 0u};
-  bool outstanding[2] = {false, false};
-  bool landing[2] = {false, false};       // (thread 0) copies issued into b, not yet seen landed
-  uint32_t land_ph[2] = {0u, 0u};          // (thread 0) the phase they complete
-  bool fail = false, ok = true, first = true;
-  int sidx = 0;
-  const unsigned char* tile = tiles + toff[blockIdx.x];
 
-  auto wait_buf = [&](int b) {
-    if (!outstanding[b]) return;
-    if (!mbar_wait(bar_done + 8u * b, ph_done[b], spin_limit)) {
-      fail = true;
-      if (tid == 0) atomicExch(err, 1);
-    }
-    ph_done[b] ^= 1u;
-    outstanding[b] = false;
-  };
-  // this thread's right-hand-side values of stage k0 of item it
-  constexpr int KH = TC_KC / 2;
-  auto load_x = [&](int it, int k0, float2* xv) {
-    const GItem I = items[it];
-    const float2* X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
-    const int kc = min(TC_KC, I.k - k0);
-#pragma unroll
-    for (int j = 0; j < KH; ++j) {
-      const int kk = half * KH + j;
-      xv[j] = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
-                                      : make_float2(0.f, 0.f);
-    }
-  };
-
-  // stages in the order of the tiles: items in order, 16 inner rows at a time
-  // (items without inner rows have no stage)
-  int it = t.it0, k0 = 0;
-  while (it < t.it1 && items[it].k <= 0) ++it;
-  float2 xv[KH];
-  if (it < t.it1) load_x(it, 0, xv);
-  while (it < t.it1 && ok) {
-    const int kI = items[it].k;
-    const int sb = sidx & 1;
-    wait_buf(sb);
-    unsigned char* sA = smem + sb * TC_STAGE;                  // X' slices
-    unsigned char* sB = sA + TC_NS * A_SLICE_BYTES;            // B' slices
-    // ---- matrix tile: three bulk copies (thread 0)
-    if (tid == 0) {
-      const uint32_t fb = bar_full + 8u * sb;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                   :: "r"(fb), "r"(TC_NS * plane) : "memory");
-      for (int q = 0; q < TC_NS; ++q)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-            :: "r"(smem_u32(sB + q * B_SLICE_BYTES)), "l"(tile + (size_t)q * plane), "r"(plane),
-               "r"(fb) : "memory");
-    }
-    landing[sb] = true;
-    land_ph[sb] = ph_full[sb];
-    tile += (size_t)TC_NS * plane;
-    // ---- X' slices of the prefetched values (thread = RHS row, halves split the rows)
-#pragma unroll
-    for (int j = 0; j < KH; ++j) {
-      const int kk = half * KH + j;
-      __nv_bfloat16 sr[TC_NS], si[TC_NS];
-      split3(xv[j].x, sr);
-      split3(xv[j].y, si);
-#pragma unroll
-      for (int q = 0; q < TC_NS; ++q)
-        *(uint32_t*)(sA + q * A_SLICE_BYTES + kmaj(row, 2 * kk)) = pack2(sr[q], si[q]);
-    }
-    // ---- next stage and its loads (in flight during this stage's MMAs)
-    int it2 = it, k2 = k0 + TC_KC;
-    if (k2 >= kI) {
-      it2 = it + 1;
-      k2 = 0;
-      while (it2 < t.it1 && items[it2].k <= 0) ++it2;
-    }
-    if (it2 < t.it1) load_x(it2, k2, xv);
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    ok = !__syncthreads_or(fail);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) break;
-    if (tid == 0) {
-      if (!mbar_wait(bar_full + 8u * sb, ph_full[sb], spin_limit)) {
-        fail = true;                  // the copies may still land: waited for at the end
-        atomicExch(err, 1);
-      } else {
-        landing[sb] = false;
-        for (int p = 0; p < TC_NS; ++p)
-          for (int q = 0; p + q < TC_NS; ++q)
-            for (int kh = 0; kh < TC_KR / 16; ++kh) {
-              uint64_t da = sdesc(smem_u32(sA + p * A_SLICE_BYTES) + kh * 256);
-              uint64_t db = sdesc(smem_u32(sB + q * B_SLICE_BYTES) + kh * 256);
-              uint32_t acc = first ? 0u : 1u;
-              first = false;
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                  :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  if (warp == 0) {
+    // ------------------------------------------------ MMA issuer (one thread)
+    if (lane == 0) {
+      int g = 0, j = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < n_tasks && !stop; u += gridDim.x) {
+        const GTask t = tasks[order[u]];
+        if (t.m <= 0) continue;
+        const int n_real = tc_nreal(t.m);
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+        const uint32_t dcol = tmem + (uint32_t)(j & 1) * 256u;
+        bool first = true;
+        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+          const int nst = tc_nst(items[it]);
+          for (int st = 0; st < nst; ++st) {
+            // accumulator half j & 1 was last used by this CTA's task j - 2
+            if (first && j >= 2 &&
+                !tc_wait(b_tempty + 8u * (j & 1), (uint32_t)(((j - 2) >> 1) & 1), spin_limit,
+                         abortp, err)) {
+              stop = true;
+              break;
             }
+            const int b = g % TC_RING;
+            const uint32_t ph = (uint32_t)((g / TC_RING) & 1);
+            if (!tc_wait(b_tile + 8u * b, ph, spin_limit, abortp, err)) {
+              stop = true;
+              break;
+            }
+            consumed_s = g + 1;
+            if (!tc_wait(b_split + 8u * b, ph, spin_limit, abortp, err)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char* sA = smem + b * TC_STAGE;
+            const uint64_t da0 = sdesc(smem_u32(sA));
+            const uint64_t db0 = sdesc(smem_u32(sA + TC_NS * A_SLICE_BYTES));
+#pragma unroll
+            for (int p = 0; p < TC_NS; ++p)
+#pragma unroll
+              for (int q = 0; p + q < TC_NS; ++q)
+#pragma unroll
+                for (int kh = 0; kh < TC_KR / 16; ++kh) {
+                  const uint64_t da = da0 + (uint64_t)((p * A_SLICE_BYTES + kh * 256) >> 4);
+                  const uint64_t db = db0 + (uint64_t)((q * B_SLICE_BYTES + kh * 256) >> 4);
+                  const uint32_t acc = first ? 0u : 1u;
+                  first = false;
+                  asm volatile(
+                      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                      :: "r"(dcol), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            tc_commit(b_empty + 8u * b);
+            ++g;
+          }
+        }
+        if (!first && !stop) {
+          tc_commit(b_tfull + 8u * (j & 1));
+          ++j;
+        }
       }
-      // always committed: a stage whose MMAs were skipped completes at once
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-          :: "r"(bar_done + 8u * sb));
     }
-    first = false;
-    if (tid != 0) landing[sb] = false;
-    ph_full[sb] ^= 1u;
-    outstanding[sb] = true;
-    ++sidx;
-    it = it2;
-    k0 = k2;
-  }
-  // MMAs and copies in flight complete before the memory is released (a
-  // limit of its own, so that a CTA that gave up still waits for them)
-  const long long lim = spin_limit > (1LL << 24) ? spin_limit : (1LL << 24);
-  for (int b = 0; b < 2; ++b) {
-    if (outstanding[b] && !mbar_wait(bar_done + 8u * b, ph_done[b], lim)) {
-      fail = true;
-      if (tid == 0) atomicExch(err, 1);
+  } else if (warp == 1) {
+    // ------------------------------------------------ matrix tiles (one thread)
+    if (lane == 0) {
+      int g = 0;
+      bool stop = false;
+      for (int u = blockIdx.x; u < n_tasks && !stop; u += gridDim.x) {
+        const GTask t = tasks[order[u]];
+        if (t.m <= 0) continue;
+        const uint32_t plane = (uint32_t)tc_nreal(t.m) * 64;
+        const unsigned char* tile = tiles + toff[order[u]];
+        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+          const int nst = tc_nst(items[it]);
+          for (int st = 0; st < nst; ++st) {
+            const int b = g % TC_RING;
+            if (g >= TC_RING &&
+                !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1),
+                         spin_limit, abortp, err)) {
+              stop = true;
+              break;
+            }
+            const uint32_t fb = b_tile + 8u * b;
+            unsigned char* sB = smem + b * TC_STAGE + TC_NS * A_SLICE_BYTES;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(fb), "r"(TC_NS * plane) : "memory");
+            for (int q = 0; q < TC_NS; ++q)
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                  :: "r"(smem_u32(sB + q * B_SLICE_BYTES)), "l"(tile + (size_t)q * plane),
+                     "r"(plane), "r"(fb) : "memory");
+            tile += (size_t)TC_NS * plane;
+            ++g;
+            armed_s = g;
+          }
+        }
+      }
     }
-    outstanding[b] = false;
-  }
-  if (tid == 0) {
-    for (int b = 0; b < 2; ++b)
-      if (landing[b] && !mbar_wait(bar_full + 8u * b, land_ph[b], lim)) atomicExch(err, 1);
-  }
-  ok = !__syncthreads_or(fail);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  // ---- epilogue: thread (warp w < 4, lane l) owns TMEM lane 32w + l = RHS row
-  if (ok && half == 0) {
-    float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
-    const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
-                                       : nullptr;
-    for (int c0 = 0; c0 < n_real; c0 += 16) {
-      uint32_t v[16];
-      uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      if (first) {
-        for (int j = 0; j < 16; ++j) v[j] = 0u;     // no inner rows: acc = 0
-      } else {
+  } else if (warp < 6) {
+    // ------------------------------------------------ right-hand-side split (128 threads)
+    const int r = tid - 64;                    // RHS row of the tile
+    const int col = y * TC_M + r;
+    // lanes of one warp store the inner rows in an order rotated by their
+    // 8-row group, so each store instruction hits 32 distinct banks
+    const int rot = (r >> 3) & 3;
+    // the next stage at or after (task u, item it, stage st)
+    auto settle = [&](int u, int it, int st) -> int3 {
+      while (u < n_tasks) {
+        const GTask t = tasks[order[u]];
+        if (t.m > 0) {
+          if (it < 0) it = t.it0;
+          while (it < t.it1) {
+            if (st < tc_nst(items[it])) return make_int3(u, it, st);
+            ++it;
+            st = 0;
+          }
+        }
+        u += gridDim.x;
+        it = -1;
+        st = 0;
+      }
+      return make_int3(u, -1, 0);
+    };
+    auto load = [&](int3 pos, float2* v) {
+      const GItem I = items[pos.y];
+      const float2* X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+      const int k0 = pos.z * TC_KC;
+      const int kc = min(TC_KC, I.k - k0);
+#pragma unroll
+      for (int j = 0; j < TC_KC; ++j) {
+        const int kk = (j + 4 * rot) & (TC_KC - 1);
+        v[j] = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
+                                       : make_float2(0.f, 0.f);
+      }
+    };
+    int g = 0;
+    bool stop = false;
+    float2 xv[TC_KC], xn[TC_KC];
+    int3 pos = settle(blockIdx.x, -1, 0);
+    if (pos.x < n_tasks) load(pos, xv);
+    while (pos.x < n_tasks && !stop) {
+      const int3 nxt = settle(pos.x, pos.y, pos.z + 1);
+      if (nxt.x < n_tasks) load(nxt, xn);
+      const int b = g % TC_RING;
+      if (g >= TC_RING &&
+          !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1), spin_limit,
+                   abortp, err)) {
+        stop = true;
+        break;
+      }
+      unsigned char* sA = smem + b * TC_STAGE;
+#pragma unroll
+      for (int j = 0; j < TC_KC; ++j) {
+        const int kk = (j + 4 * rot) & (TC_KC - 1);
+        __nv_bfloat16 sr[TC_NS], si[TC_NS];
+        split3(xv[j].x, sr);
+        split3(xv[j].y, si);
+#pragma unroll
+        for (int s = 0; s < TC_NS; ++s)
+          *(uint32_t*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = pack2(sr[s], si[s]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      tc_arrive(b_split + 8u * b);
+      ++g;
+#pragma unroll
+      for (int j = 0; j < TC_KC; ++j) xv[j] = xn[j];
+      pos = nxt;
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 6-9)
+    const int q4 = warp & 3;                   // TMEM lane quarter of this warp
+    const int r = q4 * 32 + lane;              // RHS row of the tile
+    const int col = y * TC_M + r;
+    const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
+    int j = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < n_tasks && !stop; u += gridDim.x) {
+      const GTask t = tasks[order[u]];
+      if (t.m <= 0) continue;
+      bool has = false;
+      for (int it = t.it0; it < t.it1 && !has; ++it) has = tc_nst(items[it]) > 0;
+      const int n_real = tc_nreal(t.m);
+      float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+      const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
+                                         : nullptr;
+      if (!has) {                              // no inner rows: out = base (or 0)
+        if (col < nrhs)
+          for (int i = 0; i < t.m; ++i)
+            out[(long long)i * nrhs + col] = base ? base[(long long)i * nrhs + col]
+                                                  : make_float2(0.f, 0.f);
+        continue;
+      }
+      // tcgen05.ld is warp-collective: the warp takes one verdict
+      const bool okw = tc_wait(b_tfull + 8u * (j & 1), (uint32_t)((j >> 1) & 1), spin_limit,
+                               abortp, err);
+      if (!__all_sync(0xffffffffu, okw)) {
+        stop = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t half = (uint32_t)(j & 1) * 256u;
+      for (int c0 = 0; c0 < n_real; c0 += 16) {
+        uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
+            : "r"(lane_base + half + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-      }
-      if (col < nrhs) {
-        for (int j = 0; j < 16; j += 2) {
-          int i = (c0 + j) / 2;
-          if (i >= t.m) break;
-          float2 y = make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1]));
-          if (base) {
-            float2 b = base[(long long)i * nrhs + col];
-            y.x += b.x;
-            y.y += b.y;
+        if (col < nrhs) {
+#pragma unroll
+          for (int jj = 0; jj < 16; jj += 2) {
+            const int i = (c0 + jj) / 2;
+            if (i < t.m) {
+              float2 yv = make_float2(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+              if (base) {
+                const float2 bv = base[(long long)i * nrhs + col];
+                yv.x += bv.x;
+                yv.y += bv.y;
+              }
+              out[(long long)i * nrhs + col] = yv;
+            }
           }
-          out[(long long)i * nrhs + col] = y;
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      tc_arrive(b_tempty + 8u * (j & 1));
+      ++j;
     }
+  }
+  __syncthreads();
+  if (abort_flag && tid == 0) {
+    // a CTA that gave up: its MMAs and copies complete before tensor memory
+    // and shared memory are released (bounded waits, abort flag ignored)
+    volatile int never = 0;
+    const long long lim = spin_limit > (1LL << 24) ? spin_limit : (1LL << 24);
+    tc_commit(b_fin);
+    tc_wait(b_fin, 0u, lim, &never, err);
+    for (int g = consumed_s; g < armed_s; ++g)
+      tc_wait(b_tile + 8u * (g % TC_RING), (uint32_t)((g / TC_RING) & 1), lim, &never, err);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
 }  // namespace
+
 
 bool tc_ok_for(const TaskList& tl) {
   for (const GTask& t : tl.tasks)
@@ -353,8 +480,10 @@ bool tc_ok_for(const TaskList& tl) {
 hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
   cudaFree(tl.d_tiles);
   cudaFree(tl.d_toff);
+  cudaFree(tl.d_torder);
   tl.d_tiles = nullptr;
   tl.d_toff = nullptr;
+  tl.d_torder = nullptr;
   tl.tile_bytes = 0;
   if (tl.tasks.empty() || !tc_ok_for(tl)) return HM_OK;
   std::vector<long long> off(tl.tasks.size());
@@ -370,9 +499,19 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
   HM_CUDA(cudaMemcpy(tl.d_toff, off.data(), off.size() * sizeof(long long),
                      cudaMemcpyHostToDevice));
   HM_CUDA(cudaMalloc((void**)&tl.d_tiles, std::max<long long>(total, 16)));
+  // persistent CTAs walk the tasks costliest first
+  std::vector<long long> cost(tl.tasks.size());
+  std::vector<int> ord(tl.tasks.size());
+  for (size_t q = 0; q < tl.tasks.size(); ++q) {
+    cost[q] = (q + 1 < off.size() ? off[q + 1] : total) - off[q];
+    ord[q] = (int)q;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  HM_CUDA(cudaMalloc((void**)&tl.d_torder, ord.size() * sizeof(int)));
+  HM_CUDA(cudaMemcpy(tl.d_torder, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
   k_tc_tiles<<<(unsigned)tl.tasks.size(), TC_THREADS>>>(tl.d_tasks, tl.d_items, ab, tl.d_tiles,
                                                         tl.d_toff);
-  HM_CUDA(cudaGetLastError());
+  HM_LAUNCHED();
   HM_CUDA(cudaDeviceSynchronize());
   tl.tile_bytes = (size_t)total;
   if (dev_bytes) *dev_bytes += (size_t)total + off.size() * sizeof(long long);
@@ -382,18 +521,26 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                           cudaStream_t s, long long spin_limit, int* err) {
   if (tl.tasks.empty()) return HM_OK;
-  if (!tl.d_tiles || !tl.d_toff) return HM_ERR_STATE;
+  if (!tl.d_tiles || !tl.d_toff || !tl.d_torder) return HM_ERR_STATE;
   (void)ab;
   static bool attr = false;
+  static int nsm = 0;
   if (!attr) {
     HM_CUDA(cudaFuncSetAttribute(k_tc_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TC_SMEM));
+                                 TC_GSMEM));
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
-  dim3 grid((unsigned)tl.tasks.size(), (unsigned)((nrhs + TC_M - 1) / TC_M));
-  k_tc_gather<<<grid, TC_THREADS, TC_SMEM, s>>>(tl.d_tasks, tl.d_items, vb, tl.d_tiles,
-                                                tl.d_toff, nrhs, spin_limit, err);
-  HM_CUDA(cudaGetLastError());
+  // one resident CTA per SM: the tiles of 128 RHS share the SMs
+  const int nt = (int)tl.tasks.size();
+  const int ytiles = (nrhs + TC_M - 1) / TC_M;
+  const int gx = std::max(1, std::min(nt, std::max(1, nsm / ytiles)));
+  dim3 grid((unsigned)gx, (unsigned)ytiles);
+  k_tc_gather<<<grid, TC_WTHREADS, TC_GSMEM, s>>>(tl.d_tasks, tl.d_items, tl.d_torder, nt, vb,
+                                                  tl.d_tiles, tl.d_toff, nrhs, spin_limit, err);
+  HM_LAUNCHED();
   return HM_OK;
 }
 
