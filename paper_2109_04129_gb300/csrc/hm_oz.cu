@@ -455,29 +455,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
           }
         }
       };
-      // the unit's stages in order (items without stages skipped); the loads
-      // of the next stage are in flight while this one is sliced
-      int it = t.it0, st = 0;
-      while (it < t.it1 && oz_nst(items[it]) == 0) ++it;
-      double2 av[EQ], avn[EQ];
-      int ex[EQ], exn[EQ];
-      if (it < t.it1) load(it, 0, av, ex);
-      while (it < t.it1 && !stop) {
-        const int trans = items[it].trans;
-        int it2 = it, st2 = st + 1;
+      // the unit's stages in order (items without stages skipped)
+      auto next = [&](int it, int st, int& it2, int& st2) {
+        it2 = it;
+        st2 = st + 1;
         if (st2 >= oz_nst(items[it])) {
           st2 = 0;
           ++it2;
           while (it2 < t.it1 && oz_nst(items[it2]) == 0) ++it2;
         }
-        if (it2 < t.it1) load(it2, st2, avn, exn);
+      };
+      // slice and store the stage whose values are in (av, ex)
+      auto put = [&](int it, const double2* av, const int* ex) -> bool {
+        const int trans = items[it].trans;
         const int b = g & (OZ_RING - 1);
         if (g >= OZ_RING &&
             !oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
-                     abortp, err)) {
-          stop = true;
-          break;
-        }
+                     abortp, err))
+          return false;
         unsigned char* sB = smem + b * OZ_STAGE + OZ_NS * OZ_A_BYTES;
 #pragma unroll
         for (int q = 0; q < EQ; ++q) {
@@ -505,11 +500,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         asm volatile("fence.proxy.async.shared::cta;");
         mbar_arrive(b_digs + 8u * b);
         ++g;
-#pragma unroll
-        for (int q = 0; q < EQ; ++q) {
-          av[q] = avn[q];
-          ex[q] = exn[q];
+        return true;
+      };
+      // loads of a stage are issued before the wait for its buffer
+      int it = t.it0, st = 0;
+      while (it < t.it1 && oz_nst(items[it]) == 0) ++it;
+      double2 av[EQ];
+      int ex[EQ];
+      while (it < t.it1 && !stop) {
+        load(it, st, av, ex);
+        if (!put(it, av, ex)) {
+          stop = true;
+          break;
         }
+        int it2, st2;
+        next(it, st, it2, st2);
         it = it2;
         st = st2;
       }

@@ -324,58 +324,69 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
     // lanes of one warp store the inner rows in an order rotated by their
     // 8-row group, so each store instruction hits 32 distinct banks
     const int rot = (r >> 3) & 3;
-    // the next stage at or after (task u, item it, stage st)
-    auto settle = [&](int u, int it, int st) -> int3 {
-      while (u < n_tasks) {
-        const GTask t = tasks[order[u]];
-        if (t.m > 0) {
-          if (it < 0) it = t.it0;
-          while (it < t.it1) {
-            if (st < tc_nst(items[it])) return make_int3(u, it, st);
-            ++it;
-            st = 0;
-          }
-        }
-        u += gridDim.x;
-        it = -1;
-        st = 0;
-      }
-      return make_int3(u, -1, 0);
+    // position in the CTA's stage sequence; the task and item in use are
+    // kept in registers, so moving to the next stage reads memory only when
+    // it crosses into another item or task
+    struct Pos {
+      int u, it, st, nst, it1;
+      const float2* X;     // input rows of the item
+      int k;
     };
-    auto load = [&](int3 pos, float2* v) {
-      const GItem I = items[pos.y];
-      const float2* X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
-      const int k0 = pos.z * TC_KC;
-      const int kc = min(TC_KC, I.k - k0);
+    auto enter_item = [&](Pos& p) -> bool {   // first item with stages at or after p.it
+      for (; p.it < p.it1; ++p.it) {
+        const GItem I = items[p.it];
+        p.nst = tc_nst(I);
+        if (p.nst > 0) {
+          p.X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+          p.k = I.k;
+          p.st = 0;
+          return true;
+        }
+      }
+      return false;
+    };
+    auto enter_task = [&](Pos& p) {          // first stage of task p.u or a later one
+      for (; p.u < n_tasks; p.u += gridDim.x) {
+        const GTask t = tasks[order[p.u]];
+        if (t.m <= 0) continue;
+        p.it = t.it0;
+        p.it1 = t.it1;
+        if (enter_item(p)) return;
+      }
+    };
+    auto advance = [&](Pos& p) {
+      if (++p.st < p.nst) return;
+      ++p.it;
+      if (enter_item(p)) return;
+      p.u += gridDim.x;
+      enter_task(p);
+    };
+    auto load = [&](const Pos& p, float2* v) {
+      const int k0 = p.st * TC_KC;
+      const int kc = min(TC_KC, p.k - k0);
 #pragma unroll
       for (int j = 0; j < TC_KC; ++j) {
         const int kk = (j + 4 * rot) & (TC_KC - 1);
-        v[j] = (kk < kc && col < nrhs) ? X[(long long)(k0 + kk) * nrhs + col]
+        v[j] = (kk < kc && col < nrhs) ? p.X[(long long)(k0 + kk) * nrhs + col]
                                        : make_float2(0.f, 0.f);
       }
     };
     int g = 0;
     bool stop = false;
-    float2 xv[TC_KC], xn[TC_KC];
-    int3 pos = settle(blockIdx.x, -1, 0);
-    if (pos.x < n_tasks) load(pos, xv);
-    while (pos.x < n_tasks && !stop) {
-      const int3 nxt = settle(pos.x, pos.y, pos.z + 1);
-      if (nxt.x < n_tasks) load(nxt, xn);
+    // split and store the stage held in v (stage buffer g % TC_RING)
+    auto put = [&](const float2* v) -> bool {
       const int b = g % TC_RING;
       if (g >= TC_RING &&
           !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1), spin_limit,
-                   abortp, err)) {
-        stop = true;
-        break;
-      }
+                   abortp, err))
+        return false;
       unsigned char* sA = smem + b * TC_STAGE;
 #pragma unroll
       for (int j = 0; j < TC_KC; ++j) {
         const int kk = (j + 4 * rot) & (TC_KC - 1);
         __nv_bfloat16 sr[TC_NS], si[TC_NS];
-        split3(xv[j].x, sr);
-        split3(xv[j].y, si);
+        split3(v[j].x, sr);
+        split3(v[j].y, si);
 #pragma unroll
         for (int s = 0; s < TC_NS; ++s)
           *(uint32_t*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = pack2(sr[s], si[s]);
@@ -383,8 +394,33 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       asm volatile("fence.proxy.async.shared::cta;");
       tc_arrive(b_split + 8u * b);
       ++g;
-#pragma unroll
-      for (int j = 0; j < TC_KC; ++j) xv[j] = xn[j];
+      return true;
+    };
+    // two register sets in turn: the loads of the next stage go to the set
+    // not being split, and nothing is copied between them (a copy would wait
+    // for those loads)
+    float2 xa[TC_KC], xb[TC_KC];
+    Pos pos;
+    pos.u = blockIdx.x;
+    enter_task(pos);
+    if (pos.u < n_tasks) load(pos, xa);
+    while (pos.u < n_tasks && !stop) {
+      Pos nxt = pos;
+      advance(nxt);
+      if (nxt.u < n_tasks) load(nxt, xb);
+      if (!put(xa)) {
+        stop = true;
+        break;
+      }
+      pos = nxt;
+      if (pos.u >= n_tasks) break;
+      nxt = pos;
+      advance(nxt);
+      if (nxt.u < n_tasks) load(nxt, xa);
+      if (!put(xb)) {
+        stop = true;
+        break;
+      }
       pos = nxt;
     }
   } else {
