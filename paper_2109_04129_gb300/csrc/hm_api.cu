@@ -483,6 +483,10 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
   for (int i = 0; i < NPHYS; ++i) rows[i] = (size_t)h->N;
   rows[P_SCR] = std::max<size_t>(1, std::max(h->fwd.scratch_rows, h->bwd.scratch_rows));
   rows[P_FAR] = std::max<size_t>(1, h->far_t_rows);
+  // the mixed-precision chain keeps its series panels in complex64: the FP64
+  // series panels (and the FP64 refinement copies) are not needed there
+  if (h->p.precision == HM_MIXED)
+    for (int i : {(int)P_BO, (int)P_IT, (int)P_SCR, (int)P_X0, (int)P_B0}) rows[i] = 1;
   for (int i = 0; i < NPHYS; ++i) {
     HM_CUDA(cudaMalloc((void**)&h->d_vec[i], rows[i] * nrhs * sizeof(cplx)));
     h->vec_rows[i] = rows[i];
@@ -592,13 +596,33 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
   ABufs a;
   tables(h, buf, buf, low, v, a);
   double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
+  // complex64 sweeps on the tensor cores read the sweep buffer through its
+  // split panel: split once here, then every finalize keeps it current
+  XSplit xs;
+  unsigned char* bufs[2];
+  const bool split = prec == PREC_32 && low && h->p.tensor_cores && nrhs >= 32 &&
+                     mixed_xsplit(h, &xs, bufs);
+  hm_status s;
+  if (split) {
+    s = ensure_err(h);
+    if (s) return s;
+    int ev = prof_begin(h);
+    s = launch_split((const float2*)buf, h->N, nrhs, bufs[0], xs.J[0], xs.G, h->stream);
+    prof_end(h, ev, PC_CONV, (double)h->N * nrhs * (8 + 12), 0.0);
+    if (s) return s;
+  }
   for (size_t l = 0; l < sw.part.size(); ++l) {
     int ev = prof_begin(h);
-    hm_status s = launch_any(h, sw.part[l], v, a, nrhs, prec, &cat);
+    TaskList& tl = sw.part[l];
+    if (split && tc_ok_for(tl))
+      s = launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err, &xs);
+    else
+      s = launch_any(h, tl, v, a, nrhs, prec, &cat);
     if (s) return s;
-    prof_end(h, ev, cat, tl_bytes(sw.part[l], nrhs, asz, vsz), 8.0 * sw.part[l].flops * nrhs);
+    prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
     ev = prof_begin(h);
-    s = launch_fin(sw.fin[l], v, nrhs, h->stream, prec);
+    s = split ? launch_fin_split(sw.fin[l], v, nrhs, bufs[0], xs.J[0], xs.G, h->stream)
+              : launch_fin(sw.fin[l], v, nrhs, h->stream, prec);
     if (s) return s;
     double fb = 0;
     for (const FTask& f : sw.fin[l].tasks) fb += (double)f.m * nrhs * vsz * (2 + f.s1 - f.s0);
@@ -630,9 +654,46 @@ hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, i
   return s;
 }
 
-hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
-  hm_status s = run_chain_list(h, h->far1_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
+// one far-field stage on the tensor cores with its input from a split panel
+// (written first from the complex64 panel src of `rows` rows)
+static hm_status far_stage_split(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs,
+                                 const float2* src, int rows, unsigned char* dst, long long J,
+                                 const XSplit& xs) {
+  hm_status s = ensure_err(h);
   if (s) return s;
+  int ev = prof_begin(h);
+  s = launch_split(src, rows, nrhs, dst, J, xs.G, h->stream);
+  prof_end(h, ev, PC_CONV, (double)rows * nrhs * (8 + 12), 0.0);
+  if (s) return s;
+  VBufs v;
+  ABufs a;
+  tables(h, in, out, true, v, a);
+  ev = prof_begin(h);
+  s = launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err, &xs);
+  prof_end(h, ev, PC_MX_FAR, tl_bytes(tl, nrhs, 8, 8), 8.0 * tl.flops * nrhs);
+  return s;
+}
+
+hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
+  XSplit xs;
+  unsigned char* bufs[2];
+  const bool tc = h->p.tensor_cores && nrhs >= 32 && mixed_xsplit(h, &xs, bufs);
+  hm_status s;
+  if (tc && tc_ok_for(h->far1_tl))
+    s = far_stage_split(h, h->far1_tl, in, out, nrhs, (const float2*)in, h->N, bufs[0], xs.J[0],
+                        xs);
+  else
+    s = run_chain_list(h, h->far1_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
+  if (s) return s;
+  if (tc && tc_ok_for(h->far2_tl)) {
+    // far-2 items read both the stage-1 panel and (dense blocks) the input
+    if (!tc_ok_for(h->far1_tl)) {
+      s = launch_split((const float2*)in, h->N, nrhs, bufs[0], xs.J[0], xs.G, h->stream);
+      if (s) return s;
+    }
+    return far_stage_split(h, h->far2_tl, in, out, nrhs, (const float2*)mixed_fart(h),
+                           std::max(1, h->far_t_rows), bufs[1], xs.J[1], xs);
+  }
   return run_chain_list(h, h->far2_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
 }
 }  // namespace hm

@@ -61,6 +61,7 @@ struct TaskList {
   unsigned char* d_tiles = nullptr;
   long long* d_toff = nullptr;
   int* d_torder = nullptr;   // task order of the persistent kernel, costliest first
+  bool tc_shift = false;     // tiles built for split-panel inputs
   size_t tile_bytes = 0;
   // FP64-accurate path: work units (task, 32-row pass), costliest first
   int2* d_units = nullptr;
@@ -210,10 +211,30 @@ hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
                           cudaStream_t s, const int* row_exp, const long long* exp_off,
                           const int* fexp_in, const int* fexp_far, const OzPanels& xp,
                           long long spin_limit, int* err, bool panels32 = false);
+// Split panels of tensor-core inputs that stay fixed during a launch: the three
+// bf16 slices of a complex64 panel, tiled so that a 16-row stage of one slice
+// is one contiguous block in the MMA's shared-memory layout (xs[0]: the VB_IN
+// input, xs[1]: the VB_FAR input; J and G as for OzPanels).
+struct XSplit {
+  const unsigned char* xs[2];
+  long long J[2];
+  int G;
+};
+size_t tc_split_bytes(int rows, int nrhs);
+// the split panels of a mixed-precision handle (false when not allocated)
+bool mixed_xsplit(hm_ctx* h, XSplit* xs, unsigned char** bufs);
+hm_status launch_split(const float2* V, int rows, int nrhs, unsigned char* out, long long J, int G,
+                       cudaStream_t s);
+// complex64 sweep finalize that also writes the split panel of its rows
+hm_status launch_fin_split(const FinList& fl, const VBufs& vb, int nrhs, unsigned char* xs,
+                           long long J, int G, cudaStream_t s);
+// xsp != nullptr: inputs from split panels (lists whose tiles were built shifted)
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                          cudaStream_t s, long long spin_limit, int* err);
-// pre-split the complex64 matrix operand of a tensor-core task list (set-up)
-hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes);
+                          cudaStream_t s, long long spin_limit, int* err,
+                          const XSplit* xsp = nullptr);
+// pre-split the complex64 matrix operand of a tensor-core task list (set-up);
+// shifted: stages start on 4-row boundaries of the input (split-panel inputs)
+hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool shifted = false);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s);
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,

@@ -33,6 +33,7 @@ struct Mixed {
   float2* far = nullptr;
   float2* tinv = nullptr;
   float2* v[NQ] = {nullptr};
+  unsigned char* xs[2] = {nullptr, nullptr};   // split panels of the far-field inputs
   int cap = 0;
 };
 
@@ -56,7 +57,12 @@ hm_status ensure32(hm_ctx* h, Mixed* M, int nrhs) {
   if (nrhs <= M->cap) return HM_OK;
   ++h->gen;
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
+  for (int i = 0; i < 2; ++i) dfree(M->xs[i]);
   M->cap = 0;
+  if (h->p.tensor_cores) {
+    HM_CUDA(cudaMalloc((void**)&M->xs[0], tc_split_bytes(h->N, nrhs)));
+    HM_CUDA(cudaMalloc((void**)&M->xs[1], tc_split_bytes(std::max(1, h->far_t_rows), nrhs)));
+  }
   for (int i = 0; i < NQ; ++i) {
     size_t rows = (size_t)h->N;
     if (i == Q_SCR) rows = std::max<size_t>(1, std::max(h->fwd.scratch_rows, h->bwd.scratch_rows));
@@ -128,17 +134,30 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   if (s) return s;
   if (h->has_scaling) s = to32(h->h_alpha, &M->alpha);
   if (!s && h->has_scaling) s = to32(h->h_tinv, &M->tinv);
+  if (!s && h->has_scaling) {
+    // a mixed-precision handle never runs the FP64 sweeps: their complex128
+    // coefficients stay on the host only (hm_save writes the host copies)
+    const size_t bytes = (h->h_alpha.size() + h->h_tinv.size()) * sizeof(cplx);
+    if (h->d_alpha || h->d_tinv) h->dev_bytes -= std::min(h->dev_bytes, bytes);
+    cudaFree(h->d_alpha);
+    cudaFree(h->d_tinv);
+    h->d_alpha = nullptr;
+    h->d_tinv = nullptr;
+  }
   if (s || !h->p.tensor_cores) return s;
   // bf16 slices of every complex64 matrix operand of the tensor-core lists
   ABufs a{};
   a.p[AB_FAR] = M->far;
   a.p[AB_ALPHA] = M->alpha;
   a.p[AB_TINV] = M->tinv;
+  // sweep inputs come from the split panel of the sweep buffer
   for (Sweep* sw : {&h->fwd, &h->bwd})
     for (TaskList& tl : sw->part)
-      if ((s = build_tc_tiles(tl, a, &h->dev_bytes))) return s;
-  if ((s = build_tc_tiles(h->far1_tl, a, &h->dev_bytes))) return s;
-  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes);
+      if ((s = build_tc_tiles(tl, a, &h->dev_bytes, true))) return s;
+  // the far-field inputs are fixed during a launch: they arrive as split
+  // panels, and the tiles of the far lists are built for that
+  if ((s = build_tc_tiles(h->far1_tl, a, &h->dev_bytes, true))) return s;
+  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes, true);
 }
 
 void hm_mixed_release(hm_ctx* h) {
@@ -148,6 +167,7 @@ void hm_mixed_release(hm_ctx* h) {
   dfree(M->far);
   dfree(M->tinv);
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
+  for (int i = 0; i < 2; ++i) dfree(M->xs[i]);
   delete M;
   h->mixed = nullptr;
 }
@@ -158,6 +178,19 @@ const void* mixed_far_data(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->fa
 const void* mixed_tinv(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->tinv : nullptr; }
 void* mixed_scratch(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_SCR] : nullptr; }
 void* mixed_fart(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_FAR] : nullptr; }
+// the split panels of the far-field inputs (false when not allocated)
+bool mixed_xsplit(hm_ctx* h, XSplit* xs, unsigned char** bufs) {
+  Mixed* M = (Mixed*)h->mixed;
+  if (!M || !M->xs[0] || !M->xs[1]) return false;
+  bufs[0] = M->xs[0];
+  bufs[1] = M->xs[1];
+  xs->xs[0] = M->xs[0];
+  xs->xs[1] = M->xs[1];
+  xs->J[0] = oz_row_groups(h->N);
+  xs->J[1] = oz_row_groups(std::max(1, h->far_t_rows));
+  xs->G = oz_rhs_groups(M->cap);
+  return true;
+}
 }  // namespace hm
 
 // Y (P_Y) = Z_N x and Z (P_Z) = Z_F x for x in P_XT, FP64-accurate products:

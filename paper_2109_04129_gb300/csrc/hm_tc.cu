@@ -83,11 +83,14 @@ __host__ __device__ __forceinline__ int tc_nreal(int m) { return ((2 * m + 15) /
 
 // Matrix tiles of one task: for each item and each 16-row inner stage, three
 // bf16 slice planes of B' (n_real rows x 32 real inner columns, plane stride
-// n_real x 64 bytes) in the canonical layout.
+// n_real x 64 bytes) in the canonical layout.  shifted: the stages of an item
+// start on the 4-row boundary of the input below its first row (split-panel
+// inputs); the rows the shift adds get zero entries.
 __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict__ tasks,
                                                          const GItem* __restrict__ items,
                                                          ABufs ab, unsigned char* __restrict__ tiles,
-                                                         const long long* __restrict__ toff) {
+                                                         const long long* __restrict__ toff,
+                                                         int shifted) {
   const GTask t = tasks[blockIdx.x];
   const int n_real = tc_nreal(t.m);
   const long long plane = (long long)n_real * 64;
@@ -96,8 +99,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
   for (int it = t.it0; it < t.it1; ++it) {
     const GItem I = items[it];
     const float2* A = (const float2*)ab.p[I.a_buf] + I.a_off;
-    for (int k0 = 0; k0 < I.k; k0 += TC_KC) {
-      const int kc = min(TC_KC, I.k - k0);
+    const int dl = shifted ? (I.in_row & 3) : 0;
+    const int nst = (I.k + dl + TC_KC - 1) / TC_KC;
+    for (int st = 0; st < nst; ++st) {
       for (int e = threadIdx.x; e < ne; e += TC_THREADS) {
         int i, kk;
         if (I.trans) {
@@ -107,9 +111,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
           i = e / TC_KC;
           kk = e % TC_KC;
         }
+        const int kr = st * TC_KC + kk - dl;
         float2 a = make_float2(0.f, 0.f);
-        if (i < t.m && kk < kc)
-          a = I.trans ? A[(long long)(k0 + kk) * I.lda + i] : A[(long long)i * I.lda + k0 + kk];
+        if (i < t.m && kr >= 0 && kr < I.k)
+          a = I.trans ? A[(long long)kr * I.lda + i] : A[(long long)i * I.lda + kr];
         __nv_bfloat16 ar[TC_NS], ai[TC_NS];
         split3(a.x, ar);
         split3(a.y, ai);
@@ -122,6 +127,87 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
       dst += TC_NS * plane;
     }
   }
+}
+
+// byte offset of the 16-byte row (slice p, 128-RHS tile y, 4-row group j,
+// 8-RHS group gl, RHS r8 within it) of a split panel with Y tiles, J groups
+__host__ __device__ __forceinline__ long long xs_off(int p, int Y, int y, long long J, long long j,
+                                                     int gl, int r8) {
+  return ((((long long)p * Y + y) * J + j) * 16 + gl) * 128 + r8 * 16;
+}
+
+// Split panel of V (rows x nrhs complex64, RHS fastest): thread = (4-row
+// group j, RHS r); for every slice it writes the 16-byte core-matrix row
+// (re, im) of rows 4j..4j+3.  Rows >= rows and RHS >= nrhs are zero.
+__global__ void k_split(const float2* __restrict__ V, int rows, int nrhs,
+                        unsigned char* __restrict__ out, long long J, int G) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int R8 = G * 8;
+  if (idx >= J * R8) return;
+  const int r = (int)(idx % R8);
+  const long long j = idx / R8;
+  __nv_bfloat16 d[8][TC_NS];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long row = 4 * j + c;
+    const float2 v = (row < rows && r < nrhs) ? V[row * nrhs + r] : make_float2(0.f, 0.f);
+    split3(v.x, d[2 * c]);
+    split3(v.y, d[2 * c + 1]);
+  }
+  const int Y = G / 16;
+#pragma unroll
+  for (int p = 0; p < TC_NS; ++p) {
+    uint4 w;
+    w.x = pack2(d[0][p], d[1][p]);
+    w.y = pack2(d[2][p], d[3][p]);
+    w.z = pack2(d[4][p], d[5][p]);
+    w.w = pack2(d[6][p], d[7][p]);
+    *(uint4*)(out + xs_off(p, Y, r >> 7, J, j, (r >> 3) & 15, r & 7)) = w;
+  }
+}
+
+// Sweep finalize (complex64) that also keeps the split panel of the sweep
+// buffer current: out = base + sum of the task's partial panels, and the
+// three bf16 slices of every finalized element go to its place in the split
+// panel (4-byte (re, im) pairs).
+__global__ void k_finalize_split(const FTask* __restrict__ tasks, const int* __restrict__ slots,
+                                 VBufs vb, int nrhs, unsigned char* __restrict__ xs, long long J,
+                                 int G) {
+  const FTask t = tasks[blockIdx.x];
+  const long long n = (long long)t.m * nrhs;
+  float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
+  const float2* base = (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs;
+  const float2* scr = (const float2*)vb.p[VB_SCR];
+  const int Y = G / 16;
+  for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < n;
+       e += (long long)blockDim.x * gridDim.y) {
+    float2 v = base[e];
+    for (int s = t.s0; s < t.s1; ++s) {
+      const float2 p = scr[(long long)slots[s] * nrhs + e];
+      v.x += p.x;
+      v.y += p.y;
+    }
+    out[e] = v;
+    const long long row = t.out_row + e / nrhs;
+    const int r = (int)(e % nrhs);
+    __nv_bfloat16 sr[TC_NS], si[TC_NS];
+    split3(v.x, sr);
+    split3(v.y, si);
+#pragma unroll
+    for (int q = 0; q < TC_NS; ++q)
+      *(uint32_t*)(xs + xs_off(q, Y, r >> 7, J, row >> 2, (r >> 3) & 15, r & 7) + (row & 3) * 4) =
+          pack2(sr[q], si[q]);
+  }
+}
+
+// shared-memory descriptor with explicit strides (no swizzle)
+__device__ __forceinline__ uint64_t sdesc_g(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
 }
 
 constexpr int TC_RING = 3;                 // shared-memory stages of the gather
@@ -154,7 +240,11 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                :: "r"(bar));
 }
 // the 16-row stages of an item
-__device__ __forceinline__ int tc_nst(const GItem& I) { return (I.k + TC_KC - 1) / TC_KC; }
+// the 16-row stages of an item (xs: split-panel input, stages from the
+// 4-row boundary below its first row)
+__device__ __forceinline__ int tc_nst(const GItem& I, int xs) {
+  return (I.k + (xs ? (I.in_row & 3) : 0) + TC_KC - 1) / TC_KC;
+}
 
 // Persistent, warp-specialised gather GEMM on complex64 lists.  Each CTA
 // walks its share of the tasks (costliest first) for one tile of 128 RHS:
@@ -172,7 +262,7 @@ __device__ __forceinline__ int tc_nst(const GItem& I) { return (I.k + TC_KC - 1)
 // tempty[h].  Every wait is bounded and watches a CTA-wide abort flag.
 __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
     const GTask* __restrict__ tasks, const GItem* __restrict__ items,
-    const int* __restrict__ order, int n_tasks, VBufs vb,
+    const int* __restrict__ order, int n_tasks, VBufs vb, XSplit xsp, int xs,
     const unsigned char* __restrict__ tiles, const long long* __restrict__ toff, int nrhs,
     long long spin_limit, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -232,7 +322,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         const uint32_t dcol = tmem + (uint32_t)(j & 1) * 256u;
         bool first = true;
         for (int it = t.it0; it < t.it1 && !stop; ++it) {
-          const int nst = tc_nst(items[it]);
+          const int nst = tc_nst(items[it], xs);
           for (int st = 0; st < nst; ++st) {
             // accumulator half j & 1 was last used by this CTA's task j - 2
             if (first && j >= 2 &&
@@ -248,13 +338,16 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
               break;
             }
             consumed_s = g + 1;
-            if (!tc_wait(b_split + 8u * b, ph, spin_limit, abortp, err)) {
+            if (!xs && !tc_wait(b_split + 8u * b, ph, spin_limit, abortp, err)) {
               stop = true;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char* sA = smem + b * TC_STAGE;
-            const uint64_t da0 = sdesc(smem_u32(sA));
+            // X' slices: split-panel blocks (K-adjacent core matrices 2 KB
+            // apart, 8-row groups 128 B apart) or the on-the-fly canonical tile
+            const uint64_t da0 = xs ? sdesc_g(smem_u32(sA), 2048, 128) : sdesc(smem_u32(sA));
+            const int kstep = xs ? 4096 : 256;      // bytes per 16 real inner columns
             const uint64_t db0 = sdesc(smem_u32(sA + TC_NS * A_SLICE_BYTES));
 #pragma unroll
             for (int p = 0; p < TC_NS; ++p)
@@ -262,7 +355,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
               for (int q = 0; p + q < TC_NS; ++q)
 #pragma unroll
                 for (int kh = 0; kh < TC_KR / 16; ++kh) {
-                  const uint64_t da = da0 + (uint64_t)((p * A_SLICE_BYTES + kh * 256) >> 4);
+                  const uint64_t da = da0 + (uint64_t)((p * A_SLICE_BYTES + kh * kstep) >> 4);
                   const uint64_t db = db0 + (uint64_t)((q * B_SLICE_BYTES + kh * 256) >> 4);
                   const uint32_t acc = first ? 0u : 1u;
                   first = false;
@@ -292,7 +385,10 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         const uint32_t plane = (uint32_t)tc_nreal(t.m) * 64;
         const unsigned char* tile = tiles + toff[order[u]];
         for (int it = t.it0; it < t.it1 && !stop; ++it) {
-          const int nst = tc_nst(items[it]);
+          const GItem I = items[it];
+          const int nst = tc_nst(I, xs);
+          const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
+          const long long j00 = (long long)((I.in_row - (I.in_row & 3)) >> 2);
           for (int st = 0; st < nst; ++st) {
             const int b = g % TC_RING;
             if (g >= TC_RING &&
@@ -304,12 +400,23 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
             const uint32_t fb = b_tile + 8u * b;
             unsigned char* sB = smem + b * TC_STAGE + TC_NS * A_SLICE_BYTES;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(fb), "r"(TC_NS * plane) : "memory");
+                         :: "r"(fb), "r"(TC_NS * (plane + (xs ? A_SLICE_BYTES : 0))) : "memory");
             for (int q = 0; q < TC_NS; ++q)
               asm volatile(
                   "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                   :: "r"(smem_u32(sB + q * B_SLICE_BYTES)), "l"(tile + (size_t)q * plane),
                      "r"(plane), "r"(fb) : "memory");
+            if (xs) {
+              // the stage's 16 input rows of each slice: one 8 KB block
+              const long long j0 = j00 + 4LL * st;
+              unsigned char* sA = smem + b * TC_STAGE;
+              for (int q = 0; q < TC_NS; ++q)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    :: "r"(smem_u32(sA + q * A_SLICE_BYTES)),
+                       "l"(xsp.xs[xb] + xs_off(q, xsp.G / 16, y, xsp.J[xb], j0, 0, 0)),
+                       "r"(A_SLICE_BYTES), "r"(fb) : "memory");
+            }
             tile += (size_t)TC_NS * plane;
             ++g;
             armed_s = g;
@@ -318,110 +425,112 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       }
     }
   } else if (warp < 6) {
-    // ------------------------------------------------ right-hand-side split (128 threads)
-    const int r = tid - 64;                    // RHS row of the tile
-    const int col = y * TC_M + r;
-    // lanes of one warp store the inner rows in an order rotated by their
-    // 8-row group, so each store instruction hits 32 distinct banks
-    const int rot = (r >> 3) & 3;
-    // position in the CTA's stage sequence; the task and item in use are
-    // kept in registers, so moving to the next stage reads memory only when
-    // it crosses into another item or task
-    struct Pos {
-      int u, it, st, nst, it1;
-      const float2* X;     // input rows of the item
-      int k;
-    };
-    auto enter_item = [&](Pos& p) -> bool {   // first item with stages at or after p.it
-      for (; p.it < p.it1; ++p.it) {
-        const GItem I = items[p.it];
-        p.nst = tc_nst(I);
-        if (p.nst > 0) {
-          p.X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
-          p.k = I.k;
-          p.st = 0;
-          return true;
+    if (!xs) {                               // (split-panel inputs arrive by bulk copy)
+      // ------------------------------------------------ right-hand-side split (128 threads)
+      const int r = tid - 64;                    // RHS row of the tile
+      const int col = y * TC_M + r;
+      // lanes of one warp store the inner rows in an order rotated by their
+      // 8-row group, so each store instruction hits 32 distinct banks
+      const int rot = (r >> 3) & 3;
+      // position in the CTA's stage sequence; the task and item in use are
+      // kept in registers, so moving to the next stage reads memory only when
+      // it crosses into another item or task
+      struct Pos {
+        int u, it, st, nst, it1;
+        const float2* X;     // input rows of the item
+        int k;
+      };
+      auto enter_item = [&](Pos& p) -> bool {   // first item with stages at or after p.it
+        for (; p.it < p.it1; ++p.it) {
+          const GItem I = items[p.it];
+          p.nst = tc_nst(I, xs);
+          if (p.nst > 0) {
+            p.X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
+            p.k = I.k;
+            p.st = 0;
+            return true;
+          }
         }
-      }
-      return false;
-    };
-    auto enter_task = [&](Pos& p) {          // first stage of task p.u or a later one
-      for (; p.u < n_tasks; p.u += gridDim.x) {
-        const GTask t = tasks[order[p.u]];
-        if (t.m <= 0) continue;
-        p.it = t.it0;
-        p.it1 = t.it1;
-        if (enter_item(p)) return;
-      }
-    };
-    auto advance = [&](Pos& p) {
-      if (++p.st < p.nst) return;
-      ++p.it;
-      if (enter_item(p)) return;
-      p.u += gridDim.x;
-      enter_task(p);
-    };
-    auto load = [&](const Pos& p, float2* v) {
-      const int k0 = p.st * TC_KC;
-      const int kc = min(TC_KC, p.k - k0);
-#pragma unroll
-      for (int j = 0; j < TC_KC; ++j) {
-        const int kk = (j + 4 * rot) & (TC_KC - 1);
-        v[j] = (kk < kc && col < nrhs) ? p.X[(long long)(k0 + kk) * nrhs + col]
-                                       : make_float2(0.f, 0.f);
-      }
-    };
-    int g = 0;
-    bool stop = false;
-    // split and store the stage held in v (stage buffer g % TC_RING)
-    auto put = [&](const float2* v) -> bool {
-      const int b = g % TC_RING;
-      if (g >= TC_RING &&
-          !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1), spin_limit,
-                   abortp, err))
         return false;
-      unsigned char* sA = smem + b * TC_STAGE;
-#pragma unroll
-      for (int j = 0; j < TC_KC; ++j) {
-        const int kk = (j + 4 * rot) & (TC_KC - 1);
-        __nv_bfloat16 sr[TC_NS], si[TC_NS];
-        split3(v[j].x, sr);
-        split3(v[j].y, si);
-#pragma unroll
-        for (int s = 0; s < TC_NS; ++s)
-          *(uint32_t*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = pack2(sr[s], si[s]);
+      };
+      auto enter_task = [&](Pos& p) {          // first stage of task p.u or a later one
+        for (; p.u < n_tasks; p.u += gridDim.x) {
+          const GTask t = tasks[order[p.u]];
+          if (t.m <= 0) continue;
+          p.it = t.it0;
+          p.it1 = t.it1;
+          if (enter_item(p)) return;
+        }
+      };
+      auto advance = [&](Pos& p) {
+        if (++p.st < p.nst) return;
+        ++p.it;
+        if (enter_item(p)) return;
+        p.u += gridDim.x;
+        enter_task(p);
+      };
+      auto load = [&](const Pos& p, float2* v) {
+        const int k0 = p.st * TC_KC;
+        const int kc = min(TC_KC, p.k - k0);
+  #pragma unroll
+        for (int j = 0; j < TC_KC; ++j) {
+          const int kk = (j + 4 * rot) & (TC_KC - 1);
+          v[j] = (kk < kc && col < nrhs) ? p.X[(long long)(k0 + kk) * nrhs + col]
+                                         : make_float2(0.f, 0.f);
+        }
+      };
+      int g = 0;
+      bool stop = false;
+      // split and store the stage held in v (stage buffer g % TC_RING)
+      auto put = [&](const float2* v) -> bool {
+        const int b = g % TC_RING;
+        if (g >= TC_RING &&
+            !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1), spin_limit,
+                     abortp, err))
+          return false;
+        unsigned char* sA = smem + b * TC_STAGE;
+  #pragma unroll
+        for (int j = 0; j < TC_KC; ++j) {
+          const int kk = (j + 4 * rot) & (TC_KC - 1);
+          __nv_bfloat16 sr[TC_NS], si[TC_NS];
+          split3(v[j].x, sr);
+          split3(v[j].y, si);
+  #pragma unroll
+          for (int s = 0; s < TC_NS; ++s)
+            *(uint32_t*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = pack2(sr[s], si[s]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        tc_arrive(b_split + 8u * b);
+        ++g;
+        return true;
+      };
+      // two register sets in turn: the loads of the next stage go to the set
+      // not being split, and nothing is copied between them (a copy would wait
+      // for those loads)
+      float2 xa[TC_KC], xb[TC_KC];
+      Pos pos;
+      pos.u = blockIdx.x;
+      enter_task(pos);
+      if (pos.u < n_tasks) load(pos, xa);
+      while (pos.u < n_tasks && !stop) {
+        Pos nxt = pos;
+        advance(nxt);
+        if (nxt.u < n_tasks) load(nxt, xb);
+        if (!put(xa)) {
+          stop = true;
+          break;
+        }
+        pos = nxt;
+        if (pos.u >= n_tasks) break;
+        nxt = pos;
+        advance(nxt);
+        if (nxt.u < n_tasks) load(nxt, xa);
+        if (!put(xb)) {
+          stop = true;
+          break;
+        }
+        pos = nxt;
       }
-      asm volatile("fence.proxy.async.shared::cta;");
-      tc_arrive(b_split + 8u * b);
-      ++g;
-      return true;
-    };
-    // two register sets in turn: the loads of the next stage go to the set
-    // not being split, and nothing is copied between them (a copy would wait
-    // for those loads)
-    float2 xa[TC_KC], xb[TC_KC];
-    Pos pos;
-    pos.u = blockIdx.x;
-    enter_task(pos);
-    if (pos.u < n_tasks) load(pos, xa);
-    while (pos.u < n_tasks && !stop) {
-      Pos nxt = pos;
-      advance(nxt);
-      if (nxt.u < n_tasks) load(nxt, xb);
-      if (!put(xa)) {
-        stop = true;
-        break;
-      }
-      pos = nxt;
-      if (pos.u >= n_tasks) break;
-      nxt = pos;
-      advance(nxt);
-      if (nxt.u < n_tasks) load(nxt, xa);
-      if (!put(xb)) {
-        stop = true;
-        break;
-      }
-      pos = nxt;
     }
   } else {
     // ------------------------------------------------ epilogue (warps 6-9)
@@ -435,7 +544,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       const GTask t = tasks[order[u]];
       if (t.m <= 0) continue;
       bool has = false;
-      for (int it = t.it0; it < t.it1 && !has; ++it) has = tc_nst(items[it]) > 0;
+      for (int it = t.it0; it < t.it1 && !has; ++it) has = tc_nst(items[it], xs) > 0;
       const int n_real = tc_nreal(t.m);
       float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
       const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
@@ -513,7 +622,7 @@ bool tc_ok_for(const TaskList& tl) {
   return true;
 }
 
-hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
+hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool shifted) {
   cudaFree(tl.d_tiles);
   cudaFree(tl.d_toff);
   cudaFree(tl.d_torder);
@@ -527,7 +636,10 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
   for (size_t q = 0; q < tl.tasks.size(); ++q) {
     const GTask& t = tl.tasks[q];
     long long stages = 0;
-    for (int it = t.it0; it < t.it1; ++it) stages += (tl.items[it].k + TC_KC - 1) / TC_KC;
+    for (int it = t.it0; it < t.it1; ++it) {
+      const GItem& I = tl.items[it];
+      stages += (I.k + (shifted ? (I.in_row & 3) : 0) + TC_KC - 1) / TC_KC;
+    }
     off[q] = total;
     total += stages * TC_NS * (long long)tc_nreal(t.m) * 64;
   }
@@ -546,18 +658,47 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
   HM_CUDA(cudaMalloc((void**)&tl.d_torder, ord.size() * sizeof(int)));
   HM_CUDA(cudaMemcpy(tl.d_torder, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
   k_tc_tiles<<<(unsigned)tl.tasks.size(), TC_THREADS>>>(tl.d_tasks, tl.d_items, ab, tl.d_tiles,
-                                                        tl.d_toff);
+                                                        tl.d_toff, shifted ? 1 : 0);
   HM_LAUNCHED();
   HM_CUDA(cudaDeviceSynchronize());
   tl.tile_bytes = (size_t)total;
+  tl.tc_shift = shifted;
   if (dev_bytes) *dev_bytes += (size_t)total + off.size() * sizeof(long long);
   return HM_OK;
 }
 
+size_t tc_split_bytes(int rows, int nrhs) {
+  return (size_t)TC_NS * oz_rhs_groups(nrhs) * oz_row_groups(rows) * 128;
+}
+
+hm_status launch_split(const float2* V, int rows, int nrhs, unsigned char* out, long long J, int G,
+                       cudaStream_t s) {
+  const long long n = J * G * 8;
+  k_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, rows, nrhs, out, J, G);
+  HM_LAUNCHED();
+  return HM_OK;
+}
+
+hm_status launch_fin_split(const FinList& fl, const VBufs& vb, int nrhs, unsigned char* xs,
+                           long long J, int G, cudaStream_t s) {
+  if (fl.tasks.empty()) return HM_OK;
+  int mmax = 1;
+  for (const FTask& f : fl.tasks) mmax = std::max(mmax, f.m);
+  const long long per_task = (long long)mmax * nrhs;
+  const int ny = (int)std::min<long long>(512, std::max<long long>(1, (per_task + 255) / 256));
+  k_finalize_split<<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots, vb,
+                                                                       nrhs, xs, J, G);
+  HM_LAUNCHED();
+  return HM_OK;
+}
+
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                          cudaStream_t s, long long spin_limit, int* err) {
+                          cudaStream_t s, long long spin_limit, int* err, const XSplit* xsp) {
   if (tl.tasks.empty()) return HM_OK;
   if (!tl.d_tiles || !tl.d_toff || !tl.d_torder) return HM_ERR_STATE;
+  // split-panel inputs need tiles built for them, and the reverse
+  if ((xsp != nullptr) != tl.tc_shift) return HM_ERR_STATE;
+  if (xsp && (xsp->G * 8 < nrhs || xsp->G % 16 != 0 || !xsp->xs[0])) return HM_ERR_INVALID;
   (void)ab;
   static bool attr = false;
   static int nsm = 0;
@@ -574,8 +715,10 @@ hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
   const int ytiles = (nrhs + TC_M - 1) / TC_M;
   const int gx = std::max(1, std::min(nt, std::max(1, nsm / ytiles)));
   dim3 grid((unsigned)gx, (unsigned)ytiles);
+  XSplit none{};
   k_tc_gather<<<grid, TC_WTHREADS, TC_GSMEM, s>>>(tl.d_tasks, tl.d_items, tl.d_torder, nt, vb,
-                                                  tl.d_tiles, tl.d_toff, nrhs, spin_limit, err);
+                                                  xsp ? *xsp : none, xsp ? 1 : 0, tl.d_tiles,
+                                                  tl.d_toff, nrhs, spin_limit, err);
   HM_LAUNCHED();
   return HM_OK;
 }
