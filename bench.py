@@ -488,6 +488,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     Ns = [s.N for s in sols]
+    held_gb = sum(s.stats()["device_bytes"] for s in sols) / 1e9
+    free_b, total_b = torch.cuda.mem_get_info(dev)
     nrhs_tot = sum(B.shape[0] for B in Bs)
     Xs = [torch.empty_like(B) for B in Bs]
     stream = torch.cuda.current_stream()
@@ -588,7 +590,9 @@ def run_batch(args):
                    "precision": args.precision, "ordering": args.ordering,
                    "l2": "inputs larger than L2 (all scatterers' factors), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "setup_s": round(t_setup, 1), "series_ratio_max": ratio_max},
+                   "setup_s": round(t_setup, 1), "series_ratio_max": ratio_max,
+                   "device_gb_held_by_handles_before_first_solve": round(held_gb, 1),
+                   "device_gb_free_before_first_solve": round(free_b / 1e9, 1)},
         "roofline": roof,
         "e2e": {"value": ws * nrhs_tot / t_e2e, "unit": "RHS/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

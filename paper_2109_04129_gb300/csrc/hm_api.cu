@@ -498,9 +498,17 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
     cudaFree(h->d_xdig[i]);
     h->d_xdig[i] = nullptr;
   }
-  if (h->p.precision == HM_MIXED && h->p.fp64_emulation) {
-    HM_CUDA(cudaMalloc((void**)&h->d_xdig[0], oz_panel_bytes(h->N, nrhs)));
-    HM_CUDA(cudaMalloc((void**)&h->d_xdig[1], oz_panel_bytes(std::max(1, h->far_t_rows), nrhs)));
+  // scratch panels of the mixed chain: digit panels of the FP64-accurate
+  // products and split panels of the tensor-core products share storage (every
+  // phase writes its panel at its start and no two phases overlap in a solve)
+  if (h->p.precision == HM_MIXED && (h->p.fp64_emulation || h->p.tensor_cores)) {
+    const int rws[2] = {h->N, std::max(1, h->far_t_rows)};
+    for (int i = 0; i < 2; ++i) {
+      size_t bytes = 0;
+      if (h->p.fp64_emulation) bytes = std::max(bytes, oz_panel_bytes(rws[i], nrhs));
+      if (h->p.tensor_cores) bytes = std::max(bytes, tc_split_bytes(rws[i], nrhs));
+      HM_CUDA(cudaMalloc((void**)&h->d_xdig[i], bytes));
+    }
   }
   h->cap_nrhs = nrhs;
   return HM_OK;

@@ -161,7 +161,7 @@ struct hm_ctx {
   int* d_err = nullptr;         // device status word (bounded waits that timed out)
   hm::RowExp rexp_near, rexp_far1, rexp_far2, rexp_dinv;
   int* d_fexp = nullptr;        // 2 * cap_nrhs column exponents
-  unsigned char* d_xdig[2] = {nullptr, nullptr};   // digit panels (OzPanels)
+  unsigned char* d_xdig[2] = {nullptr, nullptr};   // digit / split panels (OzPanels, XSplit)
   // profiling (hm_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> evpool;

@@ -33,7 +33,6 @@ struct Mixed {
   float2* far = nullptr;
   float2* tinv = nullptr;
   float2* v[NQ] = {nullptr};
-  unsigned char* xs[2] = {nullptr, nullptr};   // split panels of the far-field inputs
   int cap = 0;
 };
 
@@ -57,12 +56,7 @@ hm_status ensure32(hm_ctx* h, Mixed* M, int nrhs) {
   if (nrhs <= M->cap) return HM_OK;
   ++h->gen;
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
-  for (int i = 0; i < 2; ++i) dfree(M->xs[i]);
   M->cap = 0;
-  if (h->p.tensor_cores) {
-    HM_CUDA(cudaMalloc((void**)&M->xs[0], tc_split_bytes(h->N, nrhs)));
-    HM_CUDA(cudaMalloc((void**)&M->xs[1], tc_split_bytes(std::max(1, h->far_t_rows), nrhs)));
-  }
   for (int i = 0; i < NQ; ++i) {
     size_t rows = (size_t)h->N;
     if (i == Q_SCR) rows = std::max<size_t>(1, std::max(h->fwd.scratch_rows, h->bwd.scratch_rows));
@@ -167,7 +161,6 @@ void hm_mixed_release(hm_ctx* h) {
   dfree(M->far);
   dfree(M->tinv);
   for (int i = 0; i < NQ; ++i) dfree(M->v[i]);
-  for (int i = 0; i < 2; ++i) dfree(M->xs[i]);
   delete M;
   h->mixed = nullptr;
 }
@@ -179,16 +172,16 @@ const void* mixed_tinv(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->tinv :
 void* mixed_scratch(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_SCR] : nullptr; }
 void* mixed_fart(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->v[Q_FAR] : nullptr; }
 // the split panels of the far-field inputs (false when not allocated)
+// (the storage is the handle's scratch panel pair, shared with the digit panels)
 bool mixed_xsplit(hm_ctx* h, XSplit* xs, unsigned char** bufs) {
-  Mixed* M = (Mixed*)h->mixed;
-  if (!M || !M->xs[0] || !M->xs[1]) return false;
-  bufs[0] = M->xs[0];
-  bufs[1] = M->xs[1];
-  xs->xs[0] = M->xs[0];
-  xs->xs[1] = M->xs[1];
+  if (!h->mixed || !h->p.tensor_cores || !h->d_xdig[0] || !h->d_xdig[1]) return false;
+  bufs[0] = h->d_xdig[0];
+  bufs[1] = h->d_xdig[1];
+  xs->xs[0] = h->d_xdig[0];
+  xs->xs[1] = h->d_xdig[1];
   xs->J[0] = oz_row_groups(h->N);
   xs->J[1] = oz_row_groups(std::max(1, h->far_t_rows));
-  xs->G = oz_rhs_groups(M->cap);
+  xs->G = oz_rhs_groups(h->cap_nrhs);
   return true;
 }
 }  // namespace hm

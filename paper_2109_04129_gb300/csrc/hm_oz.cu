@@ -41,13 +41,13 @@
 // Kernel organisation (persistent, warp-specialised, one CTA per SM).  A work
 // unit is (task, 32-row pass); each CTA walks its share of the units,
 // costliest first, for one tile of 128 right-hand sides.  Warp 1 issues the
-// bulk copies, warps 2-3 slice the matrix digits, warp 0 (one thread) issues
+// bulk copies, warps 2-3 and 8-11 slice the matrix digits, warp 0 (one thread) issues
 // the MMAs of a stage (the matrix digit planes are stacked along N and the
 // levels spaced by the same width, so one MMA per input plane adds all of its
 // digit products into their levels: 8 to 12 MMAs for the 36 products), warps
 // 4-7 read the level accumulators out of tensor
 // memory and keep the FP64 sums.  They hand over through mbarriers: a ring of
-// four shared-memory stages (full: copies landed; digits: matrix digits
+// three shared-memory stages (full: copies landed; digits: matrix digits
 // written; empty: the MMAs that read it completed) and the tensor-memory
 // window (full: the window's MMAs completed; empty: the epilogue has read it).
 // Every wait is bounded and watches a CTA-wide abort flag; a CTA that gives up
@@ -73,13 +73,14 @@ constexpr int OZ_LV = 8;                  // levels kept (p + q <= 7)
 constexpr int OZ_RC = 32;                 // complex output rows per unit
 constexpr int OZ_N = 64;                  // MMA N columns reserved per level (2 * OZ_RC)
 constexpr int OZ_WIN = 256;               // complex inner rows per exact window
-constexpr int OZ_THREADS = 256;
-constexpr int OZ_RING = 4;                // shared-memory stages
-constexpr int OZ_BPROD = 64;              // matrix-digit producer threads (warps 2-3)
+constexpr int OZ_THREADS = 384;          // 12 warps
+constexpr int OZ_RING = 3;                // shared-memory stages
+constexpr int OZ_BPROD = 192;             // matrix-digit producer threads (warps 2-3, 8-11)
 constexpr int OZ_A_BYTES = OZ_M * OZ_KR * 2;      // one digit plane of X' (4 KB)
 constexpr int OZ_B_BYTES = OZ_N * OZ_KR * 2;      // one digit plane of B' (2 KB)
 constexpr int OZ_STAGE = OZ_NS * (OZ_A_BYTES + OZ_B_BYTES);   // 48 KB
-constexpr int OZ_SMEM = OZ_RING * OZ_STAGE + 1024;
+constexpr int OZ_ACC_BYTES = OZ_N * OZ_M * 8;   // FP64 sums of the epilogue, [column][RHS row]
+constexpr int OZ_SMEM = OZ_RING * OZ_STAGE + OZ_ACC_BYTES + 1024;
 constexpr int OZ_GROUP = 16 * 128;       // one 4-row group of a 128-RHS tile, one plane (2 KB)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
               cur = xb;
               cbase = wide ? 0u : (uint32_t)(w & 1) * 256u;
             }
-            const int b = g & (OZ_RING - 1);
+            const int b = g % OZ_RING;
             if (!oz_wait(b_full + 8u * b, (uint32_t)((g / OZ_RING) & 1), spin_limit, abortp, err)) {
               stop = true;
               break;
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
         const long long j00 = (long long)((I.in_row - (I.in_row & 3)) >> 2);
         for (int st = 0; st < nst; ++st) {
-          const int b = g & (OZ_RING - 1);
+          const int b = g % OZ_RING;
           // lane 0 waits for the stage buffer; the warp follows its verdict
           bool okw = true;
           if (lane == 0 && g >= OZ_RING)
@@ -421,9 +422,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         }
       }
     }
-  } else if (warp < 4) {
-    // ------------------------------------------------ matrix digits (64 threads)
-    const int t2 = tid - 64;
+  } else if (warp < 4 || warp >= 8) {
+    // ------------------------------------------------ matrix digits (192 threads)
+    const int t2 = warp < 4 ? tid - 64 : tid - 192;      // 0..63, 64..191
     int g = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       const int n_real = max(32, ((2 * nr + 15) / 16) * 16);
       const int ne = (n_real / 2) * OZ_KC;                 // elements of one plane
       const uint32_t pb = (uint32_t)n_real * (OZ_KR * 2);  // bytes of one plane
-      constexpr int EQ = OZ_RC * OZ_KC / OZ_BPROD;       // up to 4 elements per thread
+      constexpr int EQ = (OZ_RC * OZ_KC + OZ_BPROD - 1) / OZ_BPROD;   // up to 2 per thread
       // matrix values (and row exponents) of stage st of item it
       auto load = [&](int it, int st, double2* av, int* ex) {
         const GItem I = items[it];
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       // slice and store the stage whose values are in (av, ex)
       auto put = [&](int it, const double2* av, const int* ex) -> bool {
         const int trans = items[it].trans;
-        const int b = g & (OZ_RING - 1);
+        const int b = g % OZ_RING;
         if (g >= OZ_RING &&
             !oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
                      abortp, err))
@@ -524,6 +525,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
     const int row = tid - 128;                 // TMEM lane = RHS row of the tile
     const int col = y * OZ_M + row;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    // the FP64 sums of this thread's RHS row live in shared memory (column c
+    // at acc_s[c * OZ_M + row]: a warp touches 32 consecutive doubles)
+    double* acc_s = (double*)(smem + OZ_RING * OZ_STAGE);
     int w = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
@@ -532,9 +536,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       const int rp = U.y * OZ_RC;
       const int nr = min(OZ_RC, t.m - rp);
       const int* rexp = task_row_exp + task_exp_off[U.x] + rp;
-      double acc[OZ_N];
 #pragma unroll
-      for (int c = 0; c < OZ_N; ++c) acc[c] = 0.0;
+      for (int c = 0; c < OZ_N; ++c) acc_s[c * OZ_M + row] = 0.0;
       bool open = false;
       int win = 0, cur = -1;
       // read one completed window out of tensor memory into acc (NC columns
@@ -591,7 +594,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
           for (int j = 0; j < 8; ++j) {
             const long long V = (hi[j] << 16) + (lo[j] >> 12);
             const int sc = rx[j >> 1] + F - 14;
-            acc[c0 + j] = fma((double)V, pow2i(sc - 35), acc[c0 + j]);
+            double* a = acc_s + (c0 + j) * OZ_M + row;
+            *a = fma((double)V, pow2i(sc - 35), *a);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -632,7 +636,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
 #pragma unroll
       for (int i = 0; i < OZ_RC; ++i) {
         if (i < nr) {
-          double2 yv = make_double2(acc[2 * i], acc[2 * i + 1]);
+          double2 yv = make_double2(acc_s[(2 * i) * OZ_M + row], acc_s[(2 * i + 1) * OZ_M + row]);
           if (base) {
             const double2 bv = to_d2(base[(long long)i * nrhs + col]);
             yv.x += bv.x;
@@ -655,7 +659,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
           :: "r"(b_fin));
       oz_wait(b_fin, 0u, lim, &never, err);
       for (int g = consumed_s; g < armed_s; ++g)
-        oz_wait(b_full + 8u * (g & (OZ_RING - 1)), (uint32_t)((g / OZ_RING) & 1), lim, &never,
+        oz_wait(b_full + 8u * (g % OZ_RING), (uint32_t)((g / OZ_RING) & 1), lim, &never,
                 err);
     }
   }
