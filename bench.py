@@ -332,6 +332,9 @@ def run_native(args):
         # against the measured dense bf16 peak (sustained: timed inside a long step)
         pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         ach = flops / max(launches, 1) / avg_s / 1e12
+        # executed bf16 flops per algorithmic flop: 6 slice products (three-way
+        # split) or 36 digit products (FP64-accurate slicing)
+        xf = 6.0 if name in tensor_cats else 36.0
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                 "frac": ach / pk, "traffic": None, "kernel": name,
                 "peak_source": f"{peak_kind} bf16_tflops_sustained",
@@ -339,6 +342,7 @@ def run_native(args):
                         + ("48 bf16 flops per complex MAC (3-way split, 6 slice products, "
                            "real-expanded complex)" if name in tensor_cats else
                            "288 bf16 flops per complex MAC (8 digits, 36 slice products)"),
+                "executed_tflops": ach * xf, "executed_frac": ach * xf / pk,
                 "share": ms / tot_ms}
     elif flops > 0:
         pk = fp32_peak if name in fp32_cats else fp64_peak
