@@ -7,6 +7,7 @@
 //   b_o = Z~_N^{-1} b~ (Eq. 32), it_1 = Z~_N^{-1} R^T Z_F R b_o (Eq. 31)
 //   x = R (it_0 - it_1 + ...)  (Eq. 26, 36)
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -155,7 +156,7 @@ void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
         while (q < src[t].size() && (kk == 0 || kk + h->m[L[src[t][q].first]] <= KMAX)) {
           int s = L[src[t][q].first];
           long long ai = src[t][q].second;
-          GItem it;
+          GItem it{};
           it.a_off = h->alpha_off[ai];
           it.a_buf = AB_ALPHA;
           if (forward) {   // alpha_st is m_s x m_t; need alpha^T: trans read
@@ -202,9 +203,12 @@ hm_status row_exponents(hm_ctx* h, const TaskList& tl, RowExp& R) {
                                      : it.a_buf == AB_FAR ? &h->h_far
                                      : it.a_buf == AB_ALPHA ? &h->h_alpha : &h->h_dinv;
       const cplx* A = src->data() + it.a_off;
-      for (int i = 0; i < t.m; ++i)
+      // a row segment of a stacked task covers its rows only
+      const int i0 = it.nrow > 0 ? it.r0 : 0, i1 = it.nrow > 0 ? it.r0 + it.nrow : t.m;
+      for (int i = i0; i < i1; ++i)
         for (int k = 0; k < it.k; ++k) {
-          cplx a = it.trans ? A[(long long)k * it.lda + i] : A[(long long)i * it.lda + k];
+          const int li = i - i0;
+          cplx a = it.trans ? A[(long long)k * it.lda + li] : A[(long long)li * it.lda + k];
           int e1 = 0, e2 = 0;
           if (a.x != 0.0) { std::frexp(a.x, &e1); ex[i] = std::max(ex[i], e1); }
           if (a.y != 0.0) { std::frexp(a.y, &e2); ex[i] = std::max(ex[i], e2); }
@@ -294,7 +298,7 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
             for (auto& sp : src[t]) {
               if (gid[sp.first] == g) continue;
               const int s = L[sp.first];
-              GItem it;
+              GItem it{};
               it.a_off = h->alpha_off[sp.second];
               it.a_buf = AB_ALPHA;
               it.lda = forward ? mt : h->m[s];
@@ -339,12 +343,14 @@ hm_status build_schedules(hm_ctx* h) {
   free_sweep(h->bwd);
   free_tasks(h->dinv_tl);
   free_tasks(h->far1_tl);
+  free_tasks(h->far1s_tl);
   free_tasks(h->far2_tl);
   free_tasks(h->near_tl);
   h->fwd = Sweep();
   h->bwd = Sweep();
   h->dinv_tl = TaskList();
   h->far1_tl = TaskList();
+  h->far1s_tl = TaskList();
   h->far2_tl = TaskList();
   h->near_tl = TaskList();
   const int n = h->nl;
@@ -374,25 +380,50 @@ hm_status build_schedules(hm_ctx* h) {
     hm_status s = upload_tasks(h->dinv_tl, b);
     if (s) return s;
   }
-  // far field: stage 1 per low-rank block, stage 2 per leaf
-  std::vector<int> trow(h->far.size(), -1);
-  int nt = 0;
+  // far field: stage 1 per low-rank block, stage 2 per leaf.  The stage-1
+  // panel holds, for every low-rank block, t = V^T x (rank rows) at tA and
+  // t' = U^T x (rank rows) at tB; the rows of all blocks that read the same
+  // input cluster are contiguous, so the tensor-core engines can treat them as
+  // one stacked operator (far1s: up to 128 rows per task) and read the input
+  // once per task instead of once per block.
+  std::vector<int> tA(h->far.size(), -1), tB(h->far.size(), -1);
+  struct Seg { int bi, side; };                    // side 0: V^T x_c, 1: U^T x_r
+  std::map<std::pair<int, int>, std::vector<Seg>> by_input;   // (in_row, k) -> segments
   for (size_t bi = 0; bi < h->far.size(); ++bi) {
     const FarDesc& f = h->far[bi];
     if (f.kind != 0 || f.rank == 0) continue;
-    trow[bi] = nt;
-    GTask t1{VB_FAR, nt, f.rank, (int)h->far1_tl.items.size(), 0, 0, 0, 0};
-    h->far1_tl.items.push_back(GItem{f.offV, AB_FAR, f.rank, 1, f.n, VB_IN, f.c0});
-    t1.it1 = (int)h->far1_tl.items.size();
-    h->far1_tl.tasks.push_back(t1);
-    GTask t2{VB_FAR, nt + f.rank, f.rank, (int)h->far1_tl.items.size(), 0, 0, 0, 0};
-    h->far1_tl.items.push_back(GItem{f.offU, AB_FAR, f.rank, 1, f.m, VB_IN, f.r0});
-    t2.it1 = (int)h->far1_tl.items.size();
-    h->far1_tl.tasks.push_back(t2);
-    h->far1_tl.flops += (long long)f.rank * (f.m + f.n);
-    h->far1_tl.a_bytes += (long long)f.rank * (f.m + f.n) * 16;
-    nt += 2 * f.rank;
+    by_input[{f.c0, f.n}].push_back(Seg{(int)bi, 0});
+    by_input[{f.r0, f.m}].push_back(Seg{(int)bi, 1});
   }
+  constexpr int SROWS = 128;                      // rows of a stacked task
+  int nt = 0;
+  for (auto& kv : by_input) {
+    const int in_row = kv.first.first, k = kv.first.second;
+    size_t q = 0;
+    while (q < kv.second.size()) {
+      GTask ts{VB_FAR, nt, 0, (int)h->far1s_tl.items.size(), 0, 0, 0, 2};
+      while (q < kv.second.size() && (ts.m == 0 || ts.m + h->far[kv.second[q].bi].rank <= SROWS)) {
+        const Seg sg = kv.second[q++];
+        const FarDesc& f = h->far[sg.bi];
+        const long long off = sg.side == 0 ? f.offV : f.offU;
+        (sg.side == 0 ? tA : tB)[sg.bi] = nt + ts.m;
+        // the unstacked task of the same rows (FP64 and SIMT paths)
+        GTask t1{VB_FAR, nt + ts.m, f.rank, (int)h->far1_tl.items.size(), 0, 0, 0, 0};
+        h->far1_tl.items.push_back(GItem{off, AB_FAR, f.rank, 1, k, VB_IN, in_row});
+        t1.it1 = (int)h->far1_tl.items.size();
+        h->far1_tl.tasks.push_back(t1);
+        h->far1s_tl.items.push_back(GItem{off, AB_FAR, f.rank, 1, k, VB_IN, in_row, ts.m, f.rank});
+        ts.m += f.rank;
+        h->far1_tl.flops += (long long)f.rank * k;
+        h->far1_tl.a_bytes += (long long)f.rank * k * 16;
+      }
+      ts.it1 = (int)h->far1s_tl.items.size();
+      h->far1s_tl.tasks.push_back(ts);
+      nt += ts.m;
+    }
+  }
+  h->far1s_tl.flops = h->far1_tl.flops;
+  h->far1s_tl.a_bytes = h->far1_tl.a_bytes;
   h->far_t_rows = nt;
   std::vector<std::vector<GItem>> per_leaf(n);
   auto leaf_of = [&](long long row) {
@@ -406,7 +437,7 @@ hm_status build_schedules(hm_ctx* h) {
       if (f.kind == 0) {
         if (f.rank == 0) continue;
         per_leaf[l].push_back(GItem{f.offU + dr * f.rank, AB_FAR, f.rank, 0, f.rank, VB_FAR,
-                                    trow[bi]});
+                                    tA[bi]});
       } else {
         per_leaf[l].push_back(GItem{f.offU + dr * f.n, AB_FAR, f.n, 0, f.n, VB_IN, f.c0});
       }
@@ -416,7 +447,7 @@ hm_status build_schedules(hm_ctx* h) {
       if (f.kind == 0) {
         if (f.rank == 0) continue;
         per_leaf[l].push_back(GItem{f.offV + dc * f.rank, AB_FAR, f.rank, 0, f.rank, VB_FAR,
-                                    trow[bi] + f.rank});
+                                    tB[bi]});
       } else {
         per_leaf[l].push_back(GItem{f.offU + dc, AB_FAR, f.n, 1, f.m, VB_IN, f.r0});
       }
@@ -455,14 +486,16 @@ hm_status build_schedules(hm_ctx* h) {
     h->near_tl.tasks.push_back(t);
   }
   hm_status s = upload_tasks(h->far1_tl, b);
+  if (!s) s = upload_tasks(h->far1s_tl, b);
   if (!s) s = upload_tasks(h->far2_tl, b);
   if (!s) s = upload_tasks(h->near_tl, b);
   if (!s) s = row_exponents(h, h->near_tl, h->rexp_near);
   if (!s) s = row_exponents(h, h->far1_tl, h->rexp_far1);
+  if (!s) s = row_exponents(h, h->far1s_tl, h->rexp_far1s);
   if (!s) s = row_exponents(h, h->far2_tl, h->rexp_far2);
   if (!s && h->has_scaling) s = row_exponents(h, h->dinv_tl, h->rexp_dinv);
-  for (TaskList* tl : {&h->near_tl, &h->far1_tl, &h->far2_tl, &h->dinv_tl})
-    if (!s) s = build_oz_units(*tl, &h->dev_bytes);
+  for (TaskList* tl : {&h->near_tl, &h->far1_tl, &h->far1s_tl, &h->far2_tl, &h->dinv_tl})
+    if (!s) s = build_oz_units(*tl, &h->dev_bytes, tl == &h->far2_tl || tl == &h->near_tl);
   if (s) return s;
   h->sched_ready = true;
   ++h->gen;
@@ -687,15 +720,15 @@ hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
   unsigned char* bufs[2];
   const bool tc = h->p.tensor_cores && nrhs >= 32 && mixed_xsplit(h, &xs, bufs);
   hm_status s;
-  if (tc && tc_ok_for(h->far1_tl))
-    s = far_stage_split(h, h->far1_tl, in, out, nrhs, (const float2*)in, h->N, bufs[0], xs.J[0],
+  if (tc && tc_ok_for(h->far1s_tl))
+    s = far_stage_split(h, h->far1s_tl, in, out, nrhs, (const float2*)in, h->N, bufs[0], xs.J[0],
                         xs);
   else
     s = run_chain_list(h, h->far1_tl, in, out, nrhs, PC_MX_FAR, PREC_32, true);
   if (s) return s;
   if (tc && tc_ok_for(h->far2_tl)) {
     // far-2 items read both the stage-1 panel and (dense blocks) the input
-    if (!tc_ok_for(h->far1_tl)) {
+    if (!tc_ok_for(h->far1s_tl)) {
       s = launch_split((const float2*)in, h->N, nrhs, bufs[0], xs.J[0], xs.G, h->stream);
       if (s) return s;
     }
@@ -1238,6 +1271,7 @@ hm_status hm_destroy(hm_handle h) {
   free_sweep(h->bwd);
   free_tasks(h->dinv_tl);
   free_tasks(h->far1_tl);
+  free_tasks(h->far1s_tl);
   free_tasks(h->far2_tl);
   free_tasks(h->near_tl);
   hm_mixed_release(h);
@@ -1253,7 +1287,7 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_fexp);
   cudaFree(h->d_xdig[0]);
   cudaFree(h->d_xdig[1]);
-  for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2, &h->rexp_dinv}) {
+  for (RowExp* R : {&h->rexp_near, &h->rexp_far1, &h->rexp_far2, &h->rexp_dinv, &h->rexp_far1s}) {
     cudaFree(R->d_e);
     cudaFree(R->d_off);
   }

@@ -17,6 +17,9 @@ typedef double2 cplx;   // complex128 as (re, im)
 // A task computes one output panel of m rows x nrhs columns:
 //   acc = sum over its items of op(A_item) * in_item
 //   mode 0: out = acc        mode 1: out = base + acc
+//   mode 2 (stacked, tensor-core engines only): the items are row segments
+//     of one operator over the same input rows (those of item it0): out rows
+//     [r0, r0 + nrow) = op(A_item) * in
 // Panels live in "vector buffers" with row stride nrhs (RHS fastest).
 struct GTask {
   int out_buf, out_row, m, it0, it1, base_buf, base_row, mode;
@@ -25,7 +28,15 @@ struct GTask {
 struct GItem {
   long long a_off;
   int a_buf, lda, trans, k, in_buf, in_row;
+  // row segment of a stacked task (mode 2): this item supplies task rows
+  // [r0, r0 + nrow); nrow = 0 elsewhere (the item covers every row)
+  int r0, nrow;
 };
+// items whose inner rows a task walks: all of them, or only item it0 for a
+// stacked task (its other items are row segments over the same inner rows)
+__host__ __device__ inline int task_it_end(const GTask& t) {
+  return t.mode == 2 ? t.it0 + 1 : t.it1;
+}
 // Finalize: out = base + sum of scratch panels (rows s of slot list).
 struct FTask {
   int out_buf, out_row, m, base_buf, base_row, s0, s1;
@@ -138,6 +149,7 @@ struct hm_ctx {
   // schedules
   hm::Sweep fwd, bwd;
   hm::TaskList dinv_tl, far1_tl, far2_tl, near_tl;
+  hm::TaskList far1s_tl;   // far stage 1 stacked by source cluster (tensor-core engines)
   int far_t_rows = 0;           // rows of VB_FAR (2 * sum rank)
   bool sched_ready = false;
   // work buffers sized for cap_nrhs
@@ -159,7 +171,7 @@ struct hm_ctx {
   std::vector<int> tris, edge;
   double* d_norms = nullptr;    // 4 * cap_nrhs
   int* d_err = nullptr;         // device status word (bounded waits that timed out)
-  hm::RowExp rexp_near, rexp_far1, rexp_far2, rexp_dinv;
+  hm::RowExp rexp_near, rexp_far1, rexp_far2, rexp_dinv, rexp_far1s;
   int* d_fexp = nullptr;        // 2 * cap_nrhs column exponents
   unsigned char* d_xdig[2] = {nullptr, nullptr};   // digit / split panels (OzPanels, XSplit)
   // profiling (hm_profile_enable)
@@ -201,7 +213,7 @@ struct OzPanels {
   long long J[2];   // 4-row groups of each panel
   int G;            // 8-RHS groups of both panels
 };
-hm_status build_oz_units(TaskList& tl, size_t* dev_bytes);
+hm_status build_oz_units(TaskList& tl, size_t* dev_bytes, bool list_order = false);
 long long oz_row_groups(int rows);
 int oz_rhs_groups(int nrhs);
 size_t oz_panel_bytes(int rows, int nrhs);

@@ -150,7 +150,7 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
       if ((s = build_tc_tiles(tl, a, &h->dev_bytes, true))) return s;
   // the far-field inputs are fixed during a launch: they arrive as split
   // panels, and the tiles of the far lists are built for that
-  if ((s = build_tc_tiles(h->far1_tl, a, &h->dev_bytes, true))) return s;
+  if ((s = build_tc_tiles(h->far1s_tl, a, &h->dev_bytes, true))) return s;
   return build_tc_tiles(h->far2_tl, a, &h->dev_bytes, true);
 }
 
@@ -200,7 +200,7 @@ static hm_status residual_products(hm_ctx* h, int nrhs, bool with_far) {
     if ((s = run_oz_list(h, h->near_tl, h->rexp_near, V[P_XT], V[P_Y], nrhs, PC_NEAR)))
       return s;
     if (!with_far) return HM_OK;
-    if ((s = run_oz_list(h, h->far1_tl, h->rexp_far1, V[P_XT], nullptr, nrhs, PC_FAR1)))
+    if ((s = run_oz_list(h, h->far1s_tl, h->rexp_far1s, V[P_XT], nullptr, nrhs, PC_FAR1)))
       return s;
     const int tr = std::max(1, h->far_t_rows);
     if ((s = launch_col_exp(h->d_vec[P_FAR], tr, nrhs, h->d_fexp + h->cap_nrhs, h->stream)))

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         bool open = false;
         int win = 0, cur = -1;
         uint32_t cbase = 0;
-        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
           const GItem I = items[it];
           const int nst = oz_nst(I);
           const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
     bool stop = false;
     for (int u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
       const GTask t = tasks[units[u].x];
-      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+      for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
         const GItem I = items[it];
         const int nst = oz_nst(I);
         const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
@@ -439,6 +439,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       const uint32_t pb = (uint32_t)n_real * (OZ_KR * 2);  // bytes of one plane
       constexpr int EQ = (OZ_RC * OZ_KC + OZ_BPROD - 1) / OZ_BPROD;   // up to 2 per thread
       // matrix values (and row exponents) of stage st of item it
+      // a stacked task: the row segment (offset, lda, local row) that holds
+      // each of this thread's element rows, looked up once per unit
+      const bool stacked = t.mode == 2;
+      long long soff[EQ];
+      int slda[EQ], sli[EQ];
+      if (stacked) {
+        const int tr = items[t.it0].trans;
+#pragma unroll
+        for (int q = 0; q < EQ; ++q) {
+          int i, kk;
+          oz_elem(t2 + q * OZ_BPROD, tr, i, kk);
+          const int row = rp + i;
+          soff[q] = 0;
+          slda[q] = 0;
+          sli[q] = -1;
+          for (int sq = t.it0; sq < t.it1; ++sq) {
+            const GItem Q = items[sq];
+            if (row >= Q.r0 && row < Q.r0 + Q.nrow) {
+              soff[q] = Q.a_off;
+              slda[q] = Q.lda;
+              sli[q] = row - Q.r0;
+            }
+          }
+        }
+      }
       auto load = [&](int it, int st, double2* av, int* ex) {
         const GItem I = items[it];
         const double2* A = (const double2*)ab.p[I.a_buf] + I.a_off;
@@ -451,7 +476,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
           av[q] = make_double2(0.0, 0.0);
           ex[q] = 0;
           if (t2 + q * OZ_BPROD < ne && i < nr && kr >= 0 && kr < I.k) {
-            av[q] = I.trans ? A[(long long)kr * I.lda + rp + i] : A[(long long)(rp + i) * I.lda + kr];
+            if (stacked) {
+              if (sli[q] >= 0) {
+                const double2* S = (const double2*)ab.p[I.a_buf] + soff[q];
+                av[q] = I.trans ? S[(long long)kr * slda[q] + sli[q]]
+                                : S[(long long)sli[q] * slda[q] + kr];
+              }
+            } else {
+              av[q] = I.trans ? A[(long long)kr * I.lda + rp + i]
+                              : A[(long long)(rp + i) * I.lda + kr];
+            }
             ex[q] = rexp[i];
           }
         }
@@ -463,7 +497,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         if (st2 >= oz_nst(items[it])) {
           st2 = 0;
           ++it2;
-          while (it2 < t.it1 && oz_nst(items[it2]) == 0) ++it2;
+          while (it2 < task_it_end(t) && oz_nst(items[it2]) == 0) ++it2;
         }
       };
       // slice and store the stage whose values are in (av, ex)
@@ -505,10 +539,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       };
       // loads of a stage are issued before the wait for its buffer
       int it = t.it0, st = 0;
-      while (it < t.it1 && oz_nst(items[it]) == 0) ++it;
+      while (it < task_it_end(t) && oz_nst(items[it]) == 0) ++it;
       double2 av[EQ];
       int ex[EQ];
-      while (it < t.it1 && !stop) {
+      while (it < task_it_end(t) && !stop) {
         load(it, st, av, ex);
         if (!put(it, av, ex)) {
           stop = true;
@@ -612,7 +646,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         else
           drain_nc(std::integral_constant<int, 64>{}, xb);
       };
-      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+      for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
         const GItem I = items[it];
         const int nst = oz_nst(I);
         const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
@@ -700,7 +734,7 @@ __global__ void k_col_exp(const TV* __restrict__ V, int rows, int nrhs, int* out
 
 }  // namespace
 
-hm_status build_oz_units(TaskList& tl, size_t* dev_bytes) {
+hm_status build_oz_units(TaskList& tl, size_t* dev_bytes, bool list_order) {
   cudaFree(tl.d_units);
   tl.d_units = nullptr;
   tl.n_units = 0;
@@ -708,13 +742,16 @@ hm_status build_oz_units(TaskList& tl, size_t* dev_bytes) {
   for (size_t q = 0; q < tl.tasks.size(); ++q) {
     const GTask& t = tl.tasks[q];
     long long cost = 2;                       // set-up and output rows of a unit
-    for (int it = t.it0; it < t.it1; ++it) cost += oz_nst(tl.items[it]);
+    for (int it = t.it0; it < task_it_end(t); ++it) cost += oz_nst(tl.items[it]);
     for (int pass = 0; pass * OZ_RC < t.m; ++pass) u.push_back({cost, make_int2((int)q, pass)});
   }
-  std::stable_sort(u.begin(), u.end(), [](const std::pair<long long, int2>& a,
-                                           const std::pair<long long, int2>& b) {
-    return a.first > b.first;
-  });
+  // costliest first (load balance), or in list order: neighbouring leaf tasks
+  // read overlapping inputs, so walking them together keeps those in L2
+  if (!list_order)
+    std::stable_sort(u.begin(), u.end(), [](const std::pair<long long, int2>& a,
+                                             const std::pair<long long, int2>& b) {
+      return a.first > b.first;
+    });
   if (u.empty()) return HM_OK;
   std::vector<int2> v(u.size());
   for (size_t q = 0; q < u.size(); ++q) v[q] = u[q].second;

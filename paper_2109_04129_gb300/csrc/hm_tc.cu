@@ -96,9 +96,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
   const long long plane = (long long)n_real * 64;
   unsigned char* dst = tiles + toff[blockIdx.x];
   const int ne = (n_real / 2) * TC_KC;
-  for (int it = t.it0; it < t.it1; ++it) {
+  for (int it = t.it0; it < task_it_end(t); ++it) {
     const GItem I = items[it];
-    const float2* A = (const float2*)ab.p[I.a_buf] + I.a_off;
     const int dl = shifted ? (I.in_row & 3) : 0;
     const int nst = (I.k + dl + TC_KC - 1) / TC_KC;
     for (int st = 0; st < nst; ++st) {
@@ -112,9 +111,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
           kk = e % TC_KC;
         }
         const int kr = st * TC_KC + kk - dl;
+        // the item holding row i: this one, or the row segment of a stacked task
+        GItem S = I;
+        int li = i;
+        if (t.mode == 2) {
+          S.nrow = 0;
+          for (int q = t.it0; q < t.it1; ++q) {
+            const GItem Q = items[q];
+            if (i >= Q.r0 && i < Q.r0 + Q.nrow) {
+              S = Q;
+              li = i - Q.r0;
+            }
+          }
+          if (S.nrow == 0) li = -1;
+        }
+        const float2* A = (const float2*)ab.p[S.a_buf] + S.a_off;
         float2 a = make_float2(0.f, 0.f);
-        if (i < t.m && kr >= 0 && kr < I.k)
-          a = I.trans ? A[(long long)kr * I.lda + i] : A[(long long)i * I.lda + kr];
+        if (i < t.m && li >= 0 && kr >= 0 && kr < I.k)
+          a = S.trans ? A[(long long)kr * S.lda + li] : A[(long long)li * S.lda + kr];
         __nv_bfloat16 ar[TC_NS], ai[TC_NS];
         split3(a.x, ar);
         split3(a.y, ai);
@@ -321,7 +335,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
                                ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
         const uint32_t dcol = tmem + (uint32_t)(j & 1) * 256u;
         bool first = true;
-        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
           const int nst = tc_nst(items[it], xs);
           for (int st = 0; st < nst; ++st) {
             // accumulator half j & 1 was last used by this CTA's task j - 2
@@ -384,7 +398,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         if (t.m <= 0) continue;
         const uint32_t plane = (uint32_t)tc_nreal(t.m) * 64;
         const unsigned char* tile = tiles + toff[order[u]];
-        for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
           const GItem I = items[it];
           const int nst = tc_nst(I, xs);
           const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
           const GTask t = tasks[order[p.u]];
           if (t.m <= 0) continue;
           p.it = t.it0;
-          p.it1 = t.it1;
+          p.it1 = task_it_end(t);
           if (enter_item(p)) return;
         }
       };
@@ -544,7 +558,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       const GTask t = tasks[order[u]];
       if (t.m <= 0) continue;
       bool has = false;
-      for (int it = t.it0; it < t.it1 && !has; ++it) has = tc_nst(items[it], xs) > 0;
+      for (int it = t.it0; it < task_it_end(t) && !has; ++it) has = tc_nst(items[it], xs) > 0;
       const int n_real = tc_nreal(t.m);
       float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
       const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
@@ -636,7 +650,7 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool 
   for (size_t q = 0; q < tl.tasks.size(); ++q) {
     const GTask& t = tl.tasks[q];
     long long stages = 0;
-    for (int it = t.it0; it < t.it1; ++it) {
+    for (int it = t.it0; it < task_it_end(t); ++it) {
       const GItem& I = tl.items[it];
       stages += (I.k + (shifted ? (I.in_row & 3) : 0) + TC_KC - 1) / TC_KC;
     }
