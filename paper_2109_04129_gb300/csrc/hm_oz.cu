@@ -712,24 +712,24 @@ __device__ __forceinline__ unsigned int bexp(float v) {
   return e == 0 ? 0u : e - 127u + 1023u;
 }
 
-// F_r = smallest S with max_k max(|re|, |im|) of panel column r < 2^S
+// F_r = smallest S with max_k max(|re|, |im|) of panel column r < 2^S.
+// Thread = column r over a chunk of OZ_CE_ROWS rows (reads coalesced across
+// the threads of a warp); chunks combine by an integer atomicMax on out[r],
+// which the launcher first fills with a value below every candidate.
+constexpr int OZ_CE_ROWS = 256;
 template <class TV>
 __global__ void k_col_exp(const TV* __restrict__ V, int rows, int nrhs, int* out) {
-  __shared__ unsigned int red[256];
-  const int r = blockIdx.x;
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const long long i0 = (long long)blockIdx.x * OZ_CE_ROWS;
+  const long long i1 = min((long long)rows, i0 + OZ_CE_ROWS);
   unsigned int m = 0;      // max biased exponent seen
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    TV v = V[(long long)i * nrhs + r];
+  for (long long i = i0; i < i1; ++i) {
+    const TV v = V[i * nrhs + r];
     m = max(m, max(bexp(v.x), bexp(v.y)));
   }
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
-  }
   // |v| < 2^(e - 1022) for biased exponent e (v = 1.f * 2^(e - 1023))
-  if (threadIdx.x == 0) out[r] = red[0] == 0 ? -1022 : (int)red[0] - 1022;
+  atomicMax(out + r, m == 0 ? -1022 : (int)m - 1022);
 }
 
 }  // namespace
@@ -763,13 +763,17 @@ hm_status build_oz_units(TaskList& tl, size_t* dev_bytes, bool list_order) {
 }
 
 hm_status launch_col_exp(const cplx* V, int rows, int nrhs, int* out, cudaStream_t s) {
-  k_col_exp<double2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
+  HM_CUDA(cudaMemsetAsync(out, 0x80, sizeof(int) * nrhs, s));   // 0x80808080 < -1022
+  const dim3 grid((unsigned)((rows + OZ_CE_ROWS - 1) / OZ_CE_ROWS), (unsigned)((nrhs + 127) / 128));
+  k_col_exp<double2><<<grid, 128, 0, s>>>(V, rows, nrhs, out);
   HM_LAUNCHED();
   return HM_OK;
 }
 
 hm_status launch_col_exp32(const float2* V, int rows, int nrhs, int* out, cudaStream_t s) {
-  k_col_exp<float2><<<nrhs, 256, 0, s>>>(V, rows, nrhs, out);
+  HM_CUDA(cudaMemsetAsync(out, 0x80, sizeof(int) * nrhs, s));   // 0x80808080 < -1022
+  const dim3 grid((unsigned)((rows + OZ_CE_ROWS - 1) / OZ_CE_ROWS), (unsigned)((nrhs + 127) / 128));
+  k_col_exp<float2><<<grid, 128, 0, s>>>(V, rows, nrhs, out);
   HM_LAUNCHED();
   return HM_OK;
 }
