@@ -225,14 +225,14 @@ hm_status row_exponents(hm_ctx* h, const TaskList& tl, RowExp& R) {
 // Split the items of one target into split-K tasks (<= KMAX inner rows each),
 // partials into scratch, and add the finalize entry (in place on the target).
 void add_target(hm_ctx* h, TaskList& tl, FinList& fl, int& scr_row, int out_row, int mt,
-                const std::vector<GItem>& its) {
+                const std::vector<GItem>& its, long long kmax = KMAX) {
   if (its.empty()) return;
   FTask ft{VB_OUT, out_row, mt, VB_OUT, out_row, (int)fl.slots.size(), 0};
   size_t q = 0;
   while (q < its.size()) {
     GTask task{VB_SCR, scr_row, mt, (int)tl.items.size(), 0, 0, 0, 0};
     long long kk = 0;
-    while (q < its.size() && (kk == 0 || kk + its[q].k <= KMAX)) {
+    while (q < its.size() && (kk == 0 || kk + its[q].k <= kmax)) {
       tl.items.push_back(its[q]);
       tl.flops += (long long)mt * its[q].k;
       tl.a_bytes += (long long)mt * its[q].k * 16;
@@ -288,6 +288,8 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
       TaskList tl;
       FinList fl;
       int scr_row = 0;
+      struct Tgt { int out_row, mt; std::vector<GItem> its; };
+      std::vector<Tgt> tgts;
       for (int g : bylev[l]) {
         if (phase == 1 && !h->tg_n[g]) continue;
         const int nG = h->tg_n[g];
@@ -320,9 +322,39 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
                                     h->m[L[j]], VB_OUT, (int)h->leaf_off[L[j]]});
             }
           }
-          add_target(h, tl, fl, scr_row, (int)h->leaf_off[L[t]], mt, its);
+          tgts.push_back(Tgt{(int)h->leaf_off[L[t]], mt, std::move(its)});
         }
       }
+      // Split-K size of the phase.  The FP64 gather kernels want many small
+      // tasks (KMAX); the persistent tensor-core kernel needs only enough tasks
+      // to keep its CTAs busy, and every extra split is one more partial panel
+      // for the finalize to read: take the largest size that keeps
+      // min(TC_TASK_GOAL, tasks at KMAX) tasks.
+      long long kmax = KMAX;
+      if (h->p.precision == HM_MIXED && h->p.tensor_cores) {
+        auto count = [&](long long km) {
+          long long c = 0;
+          for (const Tgt& tg : tgts) {
+            long long kk = 0;
+            for (size_t q = 0; q < tg.its.size(); ++q) {
+              if (kk == 0 || kk + tg.its[q].k > km) {
+                ++c;
+                kk = 0;
+              }
+              kk += tg.its[q].k;
+            }
+          }
+          return c;
+        };
+        constexpr long long TC_TASK_GOAL = 300;
+        const long long goal = std::min(TC_TASK_GOAL, count(KMAX));
+        for (long long km = 4096; km > KMAX; km /= 2)
+          if (count(km) >= goal) {
+            kmax = km;
+            break;
+          }
+      }
+      for (const Tgt& tg : tgts) add_target(h, tl, fl, scr_row, tg.out_row, tg.mt, tg.its, kmax);
       max_scr = std::max(max_scr, scr_row);
       if (tl.tasks.empty()) continue;
       sw.part.push_back(std::move(tl));
