@@ -38,15 +38,17 @@
 // copies need 16-byte aligned sources): the inner rows the shift brings in
 // meet zero matrix digits and add exact zeros.
 //
-// Kernel organisation (persistent, warp-specialised, one CTA per SM).  A work
-// unit is (task, 32-row pass); each CTA walks its share of the units,
-// costliest first, for one tile of 128 right-hand sides.  Warp 1 issues the
-// bulk copies, warps 2-3 and 8-11 slice the matrix digits, warp 0 (one thread) issues
-// the MMAs of a stage (the matrix digit planes are stacked along N and the
-// levels spaced by the same width, so one MMA per input plane adds all of its
-// digit products into their levels: 8 to 12 MMAs for the 36 products), warps
-// 4-7 read the level accumulators out of tensor
-// memory and keep the FP64 sums.  They hand over through mbarriers: a ring of
+// Kernel organisation (persistent, warp-specialised, one CTA per SM, 12
+// warps).  A work unit is (task, 32-row pass); each CTA walks its share of the
+// units (costliest first, or in list order for the leaf lists) for one tile of
+// 128 right-hand sides.  Warp 1 issues the bulk copies; warps 2-3 and 8-11
+// slice the matrix digits; warp 0 (one thread) issues the MMAs of a stage
+// (the matrix digit planes are stacked along N and the levels spaced by the
+// same width, so one MMA per input plane adds all of its digit products into
+// their levels: 8 to 12 MMAs for the 36 products); warps 4-7 read the level
+// accumulators out of tensor memory and keep the FP64 sums in shared memory.
+// A stacked task (mode 2) is one operator made of row segments that share
+// the input rows.  The roles hand over through mbarriers: a ring of
 // three shared-memory stages (full: copies landed; digits: matrix digits
 // written; empty: the MMAs that read it completed) and the tensor-memory
 // window (full: the window's MMAs completed; empty: the epilogue has read it).
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         const long long j00 = (long long)((I.in_row - (I.in_row & 3)) >> 2);
         for (int st = 0; st < nst; ++st) {
           const int b = g % OZ_RING;
-          // lane 0 waits for the stage buffer; the warp follows its verdict
+          // lane 0 waits for the stage buffer; the warp follows its decision
           bool okw = true;
           if (lane == 0 && g >= OZ_RING)
             okw = oz_wait(b_empty + 8u * b, (uint32_t)(((g - OZ_RING) / OZ_RING) & 1), spin_limit,
@@ -578,7 +580,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       // per level, level stride NC)
       auto drain_nc = [&](auto ncc, int xb) {
         constexpr int NC = decltype(ncc)::value;
-        // tcgen05.ld is warp-collective: the warp takes one verdict
+        // tcgen05.ld is warp-collective: the warp takes one decision
         const bool okw = oz_wait(b_tfull + 8u * (w & 1), (uint32_t)((w >> 1) & 1), spin_limit,
                                  abortp, err);
         if (!__all_sync(0xffffffffu, okw)) {

@@ -1,8 +1,8 @@
 // Tensor-core (tcgen05) gather GEMM for the mixed-precision chain.
 //
 // Same tasks and items as the SIMT gather kernels (R^T / R sweep blocks, both
-// far-field stages), on complex64 matrices and panels.  One CTA computes one
-// task for a tile of 128 right-hand sides:
+// far-field stages; far stage 1 in its stacked form), on complex64 matrices
+// and panels.  For each task and tile of 128 right-hand sides:
 //
 //   D (128 RHS x 2m) = X' (128 x 2K) * B'^T,   B' row 2i   = [a_re, -a_im] (interleaved over k)
 //                                              B' row 2i+1 = [a_im,  a_re]
@@ -12,19 +12,15 @@
 // significant bits) and the six slice products with s_p * s_q, p + q <= 2,
 // accumulate in FP32 in tensor memory: products carry FP32-level accuracy.
 //
-// Mechanics: the matrix operand never changes between solves, so its three
-// bf16 slices are computed once at set-up (build_tc_tiles) and stored tile by
-// tile in the K-major no-swizzle canonical layout (8-row x 16-byte core
-// matrices) that the MMA reads; a stage fetches its tile with three bulk
-// copies (cp.async.bulk, completion on an mbarrier).  The right-hand sides
-// change between launches and are split on the fly, their loads issued one
-// stage ahead.  Two shared-memory stages alternate; one thread issues
-// tcgen05.mma (kind::f16, bf16 inputs, f32 accumulate, M = 128, N = 2m
-// rounded up to 16, K = 16 per instruction) and tcgen05.commit to an mbarrier
-// per stage; every wait is bounded (spin_limit), a failed wait is made
-// uniform over the CTA, recorded in *err, and the CTA returns after letting
-// its copies land and releasing its tensor memory.  The accumulator is read
-// back with tcgen05.ld (32 lanes x 32-bit per warp).
+// Operands: the matrix never changes between solves, so its three slices are
+// computed once at set-up (build_tc_tiles) and stored tile by tile in the
+// K-major no-swizzle canonical layout (8-row x 16-byte core matrices) that the
+// MMA reads.  The right-hand sides come from split panels (k_split for the
+// far-field inputs, and for the sweep buffer at the start of a sweep, kept
+// current by k_finalize_split) or, without a split panel, are split on the
+// fly.  Either way a stage arrives by bulk copies (cp.async.bulk, completion
+// on an mbarrier).  The kernel is persistent and warp-specialised; the roles,
+// barriers and bounded waits are described at k_tc_gather.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -570,7 +566,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
                                                   : make_float2(0.f, 0.f);
         continue;
       }
-      // tcgen05.ld is warp-collective: the warp takes one verdict
+      // tcgen05.ld is warp-collective: the warp takes one decision
       const bool okw = tc_wait(b_tfull + 8u * (j & 1), (uint32_t)((j >> 1) & 1), spin_limit,
                                abortp, err);
       if (!__all_sync(0xffffffffu, okw)) {
