@@ -639,15 +639,10 @@ hm_status ensure_err(hm_ctx* h) {
   return HM_OK;
 }
 
-// complex64 task lists go to the tensor-core kernel for wide RHS batches
+// CUDA-core gather in complex64 or complex128 (the tensor-core gather is
+// launched by the callers that hold split panels of the inputs)
 static hm_status launch_any(hm_ctx* h, const TaskList& tl, const VBufs& v, const ABufs& a,
-                            int nrhs, int prec, int* cat) {
-  if (prec == PREC_32 && h->p.tensor_cores && nrhs >= 32 && tc_ok_for(tl)) {
-    hm_status s = ensure_err(h);
-    if (s) return s;
-    if (cat && *cat == PC_MX_SWEEP) *cat = PC_MX_SWEEP;   // same category, tensor path
-    return launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err);
-  }
+                            int nrhs, int prec) {
   return launch_tasks(tl, v, a, nrhs, h->stream, prec);
 }
 
@@ -657,7 +652,7 @@ hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs,
   ABufs a;
   tables(h, in, out, low, v, a);
   int ev = prof_begin(h);
-  hm_status s = launch_any(h, tl, v, a, nrhs, prec, &cat);
+  hm_status s = launch_any(h, tl, v, a, nrhs, prec);
   double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
   prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
   return s;
@@ -690,7 +685,7 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
     if (split && tc_ok_for(tl))
       s = launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err, &xs);
     else
-      s = launch_any(h, tl, v, a, nrhs, prec, &cat);
+      s = launch_any(h, tl, v, a, nrhs, prec);
     if (s) return s;
     prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
     ev = prof_begin(h);

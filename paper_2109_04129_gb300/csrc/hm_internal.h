@@ -72,7 +72,6 @@ struct TaskList {
   unsigned char* d_tiles = nullptr;
   long long* d_toff = nullptr;
   int* d_torder = nullptr;   // task order of the persistent kernel, costliest first
-  bool tc_shift = false;     // tiles built for split-panel inputs
   size_t tile_bytes = 0;
   // FP64-accurate path: work units (task, 32-row pass), costliest first
   int2* d_units = nullptr;
@@ -240,13 +239,12 @@ hm_status launch_split(const float2* V, int rows, int nrhs, unsigned char* out, 
 // complex64 sweep finalize that also writes the split panel of its rows
 hm_status launch_fin_split(const FinList& fl, const VBufs& vb, int nrhs, unsigned char* xs,
                            long long J, int G, cudaStream_t s);
-// xsp != nullptr: inputs from split panels (lists whose tiles were built shifted)
+// tensor-core gather of a complex64 list whose inputs come from split panels
 hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                          cudaStream_t s, long long spin_limit, int* err,
-                          const XSplit* xsp = nullptr);
+                          cudaStream_t s, long long spin_limit, int* err, const XSplit* xsp);
 // pre-split the complex64 matrix operand of a tensor-core task list (set-up);
-// shifted: stages start on 4-row boundaries of the input (split-panel inputs)
-hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool shifted = false);
+// its stages start on the 4-row boundaries of the split panels
+hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes);
 hm_status launch_gather_perm(const cplx* B, cplx* V, const int* perm, int N, int nrhs,
                              cudaStream_t s);
 hm_status launch_scatter_perm(const cplx* V, cplx* X, const int* perm, int N, int nrhs,

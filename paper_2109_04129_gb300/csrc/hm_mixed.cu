@@ -147,11 +147,11 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   // sweep inputs come from the split panel of the sweep buffer
   for (Sweep* sw : {&h->fwd, &h->bwd})
     for (TaskList& tl : sw->part)
-      if ((s = build_tc_tiles(tl, a, &h->dev_bytes, true))) return s;
+      if ((s = build_tc_tiles(tl, a, &h->dev_bytes))) return s;
   // the far-field inputs are fixed during a launch: they arrive as split
   // panels, and the tiles of the far lists are built for that
-  if ((s = build_tc_tiles(h->far1s_tl, a, &h->dev_bytes, true))) return s;
-  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes, true);
+  if ((s = build_tc_tiles(h->far1s_tl, a, &h->dev_bytes))) return s;
+  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes);
 }
 
 void hm_mixed_release(hm_ctx* h) {

@@ -79,14 +79,13 @@ __host__ __device__ __forceinline__ int tc_nreal(int m) { return ((2 * m + 15) /
 
 // Matrix tiles of one task: for each item and each 16-row inner stage, three
 // bf16 slice planes of B' (n_real rows x 32 real inner columns, plane stride
-// n_real x 64 bytes) in the canonical layout.  shifted: the stages of an item
-// start on the 4-row boundary of the input below its first row (split-panel
-// inputs); the rows the shift adds get zero entries.
+// n_real x 64 bytes) in the canonical layout.  The stages of an item start on
+// the 4-row boundary of the input below its first row (the inputs come from
+// split panels tiled in 4-row groups); the rows the shift adds get zeros.
 __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict__ tasks,
                                                          const GItem* __restrict__ items,
                                                          ABufs ab, unsigned char* __restrict__ tiles,
-                                                         const long long* __restrict__ toff,
-                                                         int shifted) {
+                                                         const long long* __restrict__ toff) {
   const GTask t = tasks[blockIdx.x];
   const int n_real = tc_nreal(t.m);
   const long long plane = (long long)n_real * 64;
@@ -94,7 +93,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_tiles(const GTask* __restrict
   const int ne = (n_real / 2) * TC_KC;
   for (int it = t.it0; it < task_it_end(t); ++it) {
     const GItem I = items[it];
-    const int dl = shifted ? (I.in_row & 3) : 0;
+    const int dl = I.in_row & 3;
     const int nst = (I.k + dl + TC_KC - 1) / TC_KC;
     for (int st = 0; st < nst; ++st) {
       for (int e = threadIdx.x; e < ne; e += TC_THREADS) {
@@ -221,8 +220,7 @@ __device__ __forceinline__ uint64_t sdesc_g(uint32_t addr, uint32_t lbo, uint32_
 }
 
 constexpr int TC_RING = 3;                 // shared-memory stages of the gather
-constexpr int TC_XPROD = 128;              // right-hand-side split threads (warps 2-5)
-constexpr int TC_WTHREADS = 320;           // 10 warps
+constexpr int TC_WTHREADS = 192;           // 6 warps
 constexpr int TC_GSMEM = TC_RING * TC_STAGE + 1024;
 
 // bounded wait that also gives up when another role has aborted the CTA
@@ -250,10 +248,10 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                :: "r"(bar));
 }
 // the 16-row stages of an item
-// the 16-row stages of an item (xs: split-panel input, stages from the
-// 4-row boundary below its first row)
-__device__ __forceinline__ int tc_nst(const GItem& I, int xs) {
-  return (I.k + (xs ? (I.in_row & 3) : 0) + TC_KC - 1) / TC_KC;
+// the 16-row stages of an item: from the 4-row boundary of the input panel
+// below its first row (split-panel blocks start on 4-row groups)
+__device__ __forceinline__ int tc_nst(const GItem& I) {
+  return (I.k + (I.in_row & 3) + TC_KC - 1) / TC_KC;
 }
 
 // Persistent, warp-specialised gather GEMM on complex64 lists.  Each CTA
@@ -261,31 +259,29 @@ __device__ __forceinline__ int tc_nst(const GItem& I, int xs) {
 //   warp 0 (one thread) issues the 12 MMAs of a stage (6 slice products x 2 K
 //     steps) into the task's accumulator, tensor-memory half j & 1 for the
 //     CTA's j-th task, so the epilogue of one task overlaps the next task;
-//   warp 1 (one thread) fetches the stage's pre-split matrix tile (three bulk
-//     copies, completion on the stage's "tile" mbarrier);
-//   warps 2-5 split the stage's right-hand sides (thread = RHS row; loads of
-//     the next stage in flight while this one is split and stored);
-//   warps 6-9 read the accumulator (thread = TMEM lane = RHS row), add the
+//   warp 1 (one thread) fetches the stage: the pre-split matrix tile and the
+//     16 input rows of every slice of the split panel (six bulk copies,
+//     completion on the stage's "tile" mbarrier);
+//   warps 2-5 read the accumulator (thread = TMEM lane = RHS row), add the
 //     base rows and store complex64 outputs.
-// Stage buffers form a ring of TC_RING: tile[b] + split[b] full -> MMAs ->
-// empty[b]; accumulators: tfull[h] (MMAs of a task done) -> epilogue ->
-// tempty[h].  Every wait is bounded and watches a CTA-wide abort flag.
+// Stage buffers form a ring of TC_RING: tile[b] full -> MMAs -> empty[b];
+// accumulators: tfull[h] (MMAs of a task done) -> epilogue -> tempty[h].
+// Every wait is bounded and watches a CTA-wide abort flag.
 __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
     const GTask* __restrict__ tasks, const GItem* __restrict__ items,
-    const int* __restrict__ order, int n_tasks, VBufs vb, XSplit xsp, int xs,
+    const int* __restrict__ order, int n_tasks, VBufs vb, XSplit xsp,
     const unsigned char* __restrict__ tiles, const long long* __restrict__ toff, int nrhs,
     long long spin_limit, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bars[3 * TC_RING + 5];
+  __shared__ __align__(8) uint64_t bars[2 * TC_RING + 5];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int armed_s, consumed_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t b_tile = __cvta_generic_to_shared(&bars[0]);               // + 8 b
-  const uint32_t b_split = __cvta_generic_to_shared(&bars[TC_RING]);        // + 8 b
-  const uint32_t b_empty = __cvta_generic_to_shared(&bars[2 * TC_RING]);    // + 8 b
-  const uint32_t b_tfull = __cvta_generic_to_shared(&bars[3 * TC_RING]);    // + 8 h
+  const uint32_t b_empty = __cvta_generic_to_shared(&bars[TC_RING]);        // + 8 b
+  const uint32_t b_tfull = __cvta_generic_to_shared(&bars[2 * TC_RING]);    // + 8 h
   const uint32_t b_tempty = b_tfull + 16;                                    // + 8 h
   const uint32_t b_fin = b_tfull + 32;
   volatile int* abortp = &abort_flag;
@@ -293,8 +289,6 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
   if (tid == 0) {
     for (int b = 0; b < TC_RING; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_tile + 8u * b));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b_split + 8u * b),
-                   "r"(TC_XPROD));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_empty + 8u * b));
     }
     for (int h = 0; h < 2; ++h) {
@@ -332,7 +326,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         const uint32_t dcol = tmem + (uint32_t)(j & 1) * 256u;
         bool first = true;
         for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
-          const int nst = tc_nst(items[it], xs);
+          const int nst = tc_nst(items[it]);
           for (int st = 0; st < nst; ++st) {
             // accumulator half j & 1 was last used by this CTA's task j - 2
             if (first && j >= 2 &&
@@ -348,16 +342,12 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
               break;
             }
             consumed_s = g + 1;
-            if (!xs && !tc_wait(b_split + 8u * b, ph, spin_limit, abortp, err)) {
-              stop = true;
-              break;
-            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char* sA = smem + b * TC_STAGE;
             // X' slices: split-panel blocks (K-adjacent core matrices 2 KB
-            // apart, 8-row groups 128 B apart) or the on-the-fly canonical tile
-            const uint64_t da0 = xs ? sdesc_g(smem_u32(sA), 2048, 128) : sdesc(smem_u32(sA));
-            const int kstep = xs ? 4096 : 256;      // bytes per 16 real inner columns
+            // apart, 8-row groups 128 B apart)
+            const uint64_t da0 = sdesc_g(smem_u32(sA), 2048, 128);
+            constexpr int kstep = 4096;             // bytes per 16 real inner columns
             const uint64_t db0 = sdesc(smem_u32(sA + TC_NS * A_SLICE_BYTES));
 #pragma unroll
             for (int p = 0; p < TC_NS; ++p)
@@ -396,7 +386,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         const unsigned char* tile = tiles + toff[order[u]];
         for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
           const GItem I = items[it];
-          const int nst = tc_nst(I, xs);
+          const int nst = tc_nst(I);
           const int xb = (I.in_buf == VB_FAR) ? 1 : 0;
           const long long j00 = (long long)((I.in_row - (I.in_row & 3)) >> 2);
           for (int st = 0; st < nst; ++st) {
@@ -410,13 +400,13 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
             const uint32_t fb = b_tile + 8u * b;
             unsigned char* sB = smem + b * TC_STAGE + TC_NS * A_SLICE_BYTES;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         :: "r"(fb), "r"(TC_NS * (plane + (xs ? A_SLICE_BYTES : 0))) : "memory");
+                         :: "r"(fb), "r"(TC_NS * (plane + A_SLICE_BYTES)) : "memory");
             for (int q = 0; q < TC_NS; ++q)
               asm volatile(
                   "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                   :: "r"(smem_u32(sB + q * B_SLICE_BYTES)), "l"(tile + (size_t)q * plane),
                      "r"(plane), "r"(fb) : "memory");
-            if (xs) {
+            {
               // the stage's 16 input rows of each slice: one 8 KB block
               const long long j0 = j00 + 4LL * st;
               unsigned char* sA = smem + b * TC_STAGE;
@@ -434,116 +424,8 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         }
       }
     }
-  } else if (warp < 6) {
-    if (!xs) {                               // (split-panel inputs arrive by bulk copy)
-      // ------------------------------------------------ right-hand-side split (128 threads)
-      const int r = tid - 64;                    // RHS row of the tile
-      const int col = y * TC_M + r;
-      // lanes of one warp store the inner rows in an order rotated by their
-      // 8-row group, so each store instruction hits 32 distinct banks
-      const int rot = (r >> 3) & 3;
-      // position in the CTA's stage sequence; the task and item in use are
-      // kept in registers, so moving to the next stage reads memory only when
-      // it crosses into another item or task
-      struct Pos {
-        int u, it, st, nst, it1;
-        const float2* X;     // input rows of the item
-        int k;
-      };
-      auto enter_item = [&](Pos& p) -> bool {   // first item with stages at or after p.it
-        for (; p.it < p.it1; ++p.it) {
-          const GItem I = items[p.it];
-          p.nst = tc_nst(I, xs);
-          if (p.nst > 0) {
-            p.X = (const float2*)vb.p[I.in_buf] + (long long)I.in_row * nrhs;
-            p.k = I.k;
-            p.st = 0;
-            return true;
-          }
-        }
-        return false;
-      };
-      auto enter_task = [&](Pos& p) {          // first stage of task p.u or a later one
-        for (; p.u < n_tasks; p.u += gridDim.x) {
-          const GTask t = tasks[order[p.u]];
-          if (t.m <= 0) continue;
-          p.it = t.it0;
-          p.it1 = task_it_end(t);
-          if (enter_item(p)) return;
-        }
-      };
-      auto advance = [&](Pos& p) {
-        if (++p.st < p.nst) return;
-        ++p.it;
-        if (enter_item(p)) return;
-        p.u += gridDim.x;
-        enter_task(p);
-      };
-      auto load = [&](const Pos& p, float2* v) {
-        const int k0 = p.st * TC_KC;
-        const int kc = min(TC_KC, p.k - k0);
-  #pragma unroll
-        for (int j = 0; j < TC_KC; ++j) {
-          const int kk = (j + 4 * rot) & (TC_KC - 1);
-          v[j] = (kk < kc && col < nrhs) ? p.X[(long long)(k0 + kk) * nrhs + col]
-                                         : make_float2(0.f, 0.f);
-        }
-      };
-      int g = 0;
-      bool stop = false;
-      // split and store the stage held in v (stage buffer g % TC_RING)
-      auto put = [&](const float2* v) -> bool {
-        const int b = g % TC_RING;
-        if (g >= TC_RING &&
-            !tc_wait(b_empty + 8u * b, (uint32_t)(((g - TC_RING) / TC_RING) & 1), spin_limit,
-                     abortp, err))
-          return false;
-        unsigned char* sA = smem + b * TC_STAGE;
-  #pragma unroll
-        for (int j = 0; j < TC_KC; ++j) {
-          const int kk = (j + 4 * rot) & (TC_KC - 1);
-          __nv_bfloat16 sr[TC_NS], si[TC_NS];
-          split3(v[j].x, sr);
-          split3(v[j].y, si);
-  #pragma unroll
-          for (int s = 0; s < TC_NS; ++s)
-            *(uint32_t*)(sA + s * A_SLICE_BYTES + kmaj(r, 2 * kk)) = pack2(sr[s], si[s]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        tc_arrive(b_split + 8u * b);
-        ++g;
-        return true;
-      };
-      // two register sets in turn: the loads of the next stage go to the set
-      // not being split, and nothing is copied between them (a copy would wait
-      // for those loads)
-      float2 xa[TC_KC], xb[TC_KC];
-      Pos pos;
-      pos.u = blockIdx.x;
-      enter_task(pos);
-      if (pos.u < n_tasks) load(pos, xa);
-      while (pos.u < n_tasks && !stop) {
-        Pos nxt = pos;
-        advance(nxt);
-        if (nxt.u < n_tasks) load(nxt, xb);
-        if (!put(xa)) {
-          stop = true;
-          break;
-        }
-        pos = nxt;
-        if (pos.u >= n_tasks) break;
-        nxt = pos;
-        advance(nxt);
-        if (nxt.u < n_tasks) load(nxt, xa);
-        if (!put(xb)) {
-          stop = true;
-          break;
-        }
-        pos = nxt;
-      }
-    }
   } else {
-    // ------------------------------------------------ epilogue (warps 6-9)
+    // ------------------------------------------------ epilogue (warps 2-5)
     const int q4 = warp & 3;                   // TMEM lane quarter of this warp
     const int r = q4 * 32 + lane;              // RHS row of the tile
     const int col = y * TC_M + r;
@@ -554,7 +436,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       const GTask t = tasks[order[u]];
       if (t.m <= 0) continue;
       bool has = false;
-      for (int it = t.it0; it < task_it_end(t) && !has; ++it) has = tc_nst(items[it], xs) > 0;
+      for (int it = t.it0; it < task_it_end(t) && !has; ++it) has = tc_nst(items[it]) > 0;
       const int n_real = tc_nreal(t.m);
       float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
       const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
@@ -632,7 +514,7 @@ bool tc_ok_for(const TaskList& tl) {
   return true;
 }
 
-hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool shifted) {
+hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes) {
   cudaFree(tl.d_tiles);
   cudaFree(tl.d_toff);
   cudaFree(tl.d_torder);
@@ -648,7 +530,7 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool 
     long long stages = 0;
     for (int it = t.it0; it < task_it_end(t); ++it) {
       const GItem& I = tl.items[it];
-      stages += (I.k + (shifted ? (I.in_row & 3) : 0) + TC_KC - 1) / TC_KC;
+      stages += (I.k + (I.in_row & 3) + TC_KC - 1) / TC_KC;
     }
     off[q] = total;
     total += stages * TC_NS * (long long)tc_nreal(t.m) * 64;
@@ -668,11 +550,10 @@ hm_status build_tc_tiles(TaskList& tl, const ABufs& ab, size_t* dev_bytes, bool 
   HM_CUDA(cudaMalloc((void**)&tl.d_torder, ord.size() * sizeof(int)));
   HM_CUDA(cudaMemcpy(tl.d_torder, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
   k_tc_tiles<<<(unsigned)tl.tasks.size(), TC_THREADS>>>(tl.d_tasks, tl.d_items, ab, tl.d_tiles,
-                                                        tl.d_toff, shifted ? 1 : 0);
+                                                        tl.d_toff);
   HM_LAUNCHED();
   HM_CUDA(cudaDeviceSynchronize());
   tl.tile_bytes = (size_t)total;
-  tl.tc_shift = shifted;
   if (dev_bytes) *dev_bytes += (size_t)total + off.size() * sizeof(long long);
   return HM_OK;
 }
@@ -706,9 +587,8 @@ hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
                           cudaStream_t s, long long spin_limit, int* err, const XSplit* xsp) {
   if (tl.tasks.empty()) return HM_OK;
   if (!tl.d_tiles || !tl.d_toff || !tl.d_torder) return HM_ERR_STATE;
-  // split-panel inputs need tiles built for them, and the reverse
-  if ((xsp != nullptr) != tl.tc_shift) return HM_ERR_STATE;
-  if (xsp && (xsp->G * 8 < nrhs || xsp->G % 16 != 0 || !xsp->xs[0])) return HM_ERR_INVALID;
+  // the right-hand sides come from split panels
+  if (!xsp || xsp->G * 8 < nrhs || xsp->G % 16 != 0 || !xsp->xs[0]) return HM_ERR_INVALID;
   (void)ab;
   static bool attr = false;
   static int nsm = 0;
@@ -725,10 +605,9 @@ hm_status launch_tasks_tc(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
   const int ytiles = (nrhs + TC_M - 1) / TC_M;
   const int gx = std::max(1, std::min(nt, std::max(1, nsm / ytiles)));
   dim3 grid((unsigned)gx, (unsigned)ytiles);
-  XSplit none{};
   k_tc_gather<<<grid, TC_WTHREADS, TC_GSMEM, s>>>(tl.d_tasks, tl.d_items, tl.d_torder, nt, vb,
-                                                  xsp ? *xsp : none, xsp ? 1 : 0, tl.d_tiles,
-                                                  tl.d_toff, nrhs, spin_limit, err);
+                                                  *xsp, tl.d_tiles, tl.d_toff, nrhs, spin_limit,
+                                                  err);
   HM_LAUNCHED();
   return HM_OK;
 }
