@@ -17,9 +17,8 @@
 // K-major no-swizzle canonical layout (8-row x 16-byte core matrices) that the
 // MMA reads.  The right-hand sides come from split panels (k_split for the
 // far-field inputs, and for the sweep buffer at the start of a sweep, kept
-// current by k_finalize_split) or, without a split panel, are split on the
-// fly.  Either way a stage arrives by bulk copies (cp.async.bulk, completion
-// on an mbarrier).  The kernel is persistent and warp-specialised; the roles,
+// current by k_finalize_split).  A stage of both operands arrives by bulk
+// copies (cp.async.bulk, completion on an mbarrier).  The kernel is persistent and warp-specialised; the roles,
 // barriers and bounded waits are described at k_tc_gather.
 #include <cuda_bf16.h>
 
@@ -37,7 +36,7 @@ constexpr int TC_KC = 16;        // complex inner rows per stage (K = 32 real)
 constexpr int TC_KR = 2 * TC_KC;
 constexpr int TC_NS = 3;         // bf16 slices per operand
 constexpr int TC_NMAX = 256;     // max MMA N (2 * 128 complex rows)
-constexpr int TC_THREADS = 256;     // two halves share the staging; warps 0-3 own TMEM rows
+constexpr int TC_THREADS = 256;  // threads of the set-up tile builder
 constexpr int A_SLICE_BYTES = TC_M * TC_KR * 2;       // 8 KB
 constexpr int B_SLICE_BYTES = TC_NMAX * TC_KR * 2;    // 16 KB
 constexpr int TC_STAGE = TC_NS * (A_SLICE_BYTES + B_SLICE_BYTES);   // 72 KB
@@ -247,7 +246,6 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                :: "r"(bar));
 }
-// the 16-row stages of an item
 // the 16-row stages of an item: from the 4-row boundary of the input panel
 // below its first row (split-panel blocks start on 4-row groups)
 __device__ __forceinline__ int tc_nst(const GItem& I) {
