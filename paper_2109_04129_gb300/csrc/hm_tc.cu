@@ -178,33 +178,58 @@ __global__ void k_split(const float2* __restrict__ V, int rows, int nrhs,
 // buffer current: out = base + sum of the task's partial panels, and the
 // three bf16 slices of every finalized element go to its place in the split
 // panel (4-byte (re, im) pairs).
+// Each thread finalizes FIN_EPT elements of the target, FIN_EPT apart by the
+// grid stride, and issues the loads of all of them before it adds: the
+// partials of one element are summed in slot order, as a plain loop would.
+constexpr int FIN_EPT = 4;
 __global__ void k_finalize_split(const FTask* __restrict__ tasks, const int* __restrict__ slots,
                                  VBufs vb, int nrhs, unsigned char* __restrict__ xs, long long J,
                                  int G) {
   const FTask t = tasks[blockIdx.x];
   const long long n = (long long)t.m * nrhs;
+  const long long e0 = threadIdx.x + (long long)blockIdx.y * blockDim.x;
+  if (e0 >= n) return;
+  const long long stride = (long long)blockDim.x * gridDim.y;
   float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
   const float2* base = (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs;
   const float2* scr = (const float2*)vb.p[VB_SCR];
   const int Y = G / 16;
-  for (long long e = threadIdx.x + (long long)blockIdx.y * blockDim.x; e < n;
-       e += (long long)blockDim.x * gridDim.y) {
-    float2 v = base[e];
-    for (int s = t.s0; s < t.s1; ++s) {
-      const float2 p = scr[(long long)slots[s] * nrhs + e];
-      v.x += p.x;
-      v.y += p.y;
-    }
-    out[e] = v;
-    const long long row = t.out_row + e / nrhs;
-    const int r = (int)(e % nrhs);
-    __nv_bfloat16 sr[TC_NS], si[TC_NS];
-    split3(v.x, sr);
-    split3(v.y, si);
+  for (long long ea = e0; ea < n; ea += FIN_EPT * stride) {
+    float2 v[FIN_EPT];
 #pragma unroll
-    for (int q = 0; q < TC_NS; ++q)
-      *(uint32_t*)(xs + xs_off(q, Y, r >> 7, J, row >> 2, (r >> 3) & 15, r & 7) + (row & 3) * 4) =
-          pack2(sr[q], si[q]);
+    for (int k = 0; k < FIN_EPT; ++k) {
+      const long long e = ea + k * stride;
+      v[k] = e < n ? base[e] : make_float2(0.f, 0.f);
+    }
+    for (int s = t.s0; s < t.s1; ++s) {
+      const float2* P = scr + (long long)slots[s] * nrhs;
+      float2 p[FIN_EPT];
+#pragma unroll
+      for (int k = 0; k < FIN_EPT; ++k) {
+        const long long e = ea + k * stride;
+        p[k] = e < n ? P[e] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < FIN_EPT; ++k) {
+        v[k].x += p[k].x;
+        v[k].y += p[k].y;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < FIN_EPT; ++k) {
+      const long long e = ea + k * stride;
+      if (e >= n) break;
+      out[e] = v[k];
+      const long long row = t.out_row + e / nrhs;
+      const int r = (int)(e % nrhs);
+      __nv_bfloat16 sr[TC_NS], si[TC_NS];
+      split3(v[k].x, sr);
+      split3(v[k].y, si);
+#pragma unroll
+      for (int q = 0; q < TC_NS; ++q)
+        *(uint32_t*)(xs + xs_off(q, Y, r >> 7, J, row >> 2, (r >> 3) & 15, r & 7) +
+                     (row & 3) * 4) = pack2(sr[q], si[q]);
+    }
   }
 }
 
@@ -574,7 +599,9 @@ hm_status launch_fin_split(const FinList& fl, const VBufs& vb, int nrhs, unsigne
   int mmax = 1;
   for (const FTask& f : fl.tasks) mmax = std::max(mmax, f.m);
   const long long per_task = (long long)mmax * nrhs;
-  const int ny = (int)std::min<long long>(512, std::max<long long>(1, (per_task + 255) / 256));
+  const long long per_block = 256LL * FIN_EPT;
+  const int ny = (int)std::min<long long>(512, std::max<long long>(1, (per_task + per_block - 1) /
+                                                                          per_block));
   k_finalize_split<<<dim3((unsigned)fl.tasks.size(), ny), 256, 0, s>>>(fl.d_tasks, fl.d_slots, vb,
                                                                        nrhs, xs, J, G);
   HM_LAUNCHED();
