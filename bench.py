@@ -27,6 +27,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "power-series RHS solves/s at rel.err ≤1e-4 vs FP64; mixed vs FP64 on 1 GB300"
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# FP64-accurate residual far-field kernels, from one ncu capture of this bench
+# (2-lambda sphere, 362 RHS, mixed precision; summary under profiles/).  They
+# are reported as the roofline's "traffic" only while the kernel's source file
+# still hashes to the captured version; any later edit turns them off (null).
+NCU_TRAFFIC_SOURCE = ("paper_2109_04129_gb300/csrc/hm_oz.cu",
+                      "7a99870e0debacda4a580de2aa214aa611378f25ffecad0bf6e233810afe66d4")
+NCU_TRAFFIC = {("sphere_r2_L5", "mixed", 362, "far_stage1"): 2.230756e9 + 1.990304e9,
+               ("sphere_r2_L5", "mixed", 362, "far_stage2"): 30.976054e9 + 0.187359e9}
+
+
+def captured_traffic(workload, precision, nrhs, kernel):
+    """ncu DRAM bytes per launch of `kernel`, or None when not captured for this
+    configuration or when the kernel source changed since the capture."""
+    b = NCU_TRAFFIC.get((workload, precision, nrhs, kernel))
+    if b is None:
+        return None
+    import hashlib
+    with open(os.path.join(ROOT, NCU_TRAFFIC_SOURCE[0]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != NCU_TRAFFIC_SOURCE[1]:
+            return None
+    return b
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -336,7 +359,9 @@ def run_native(args):
         # split) or 36 digit products (FP64-accurate slicing)
         xf = 6.0 if name in tensor_cats else 36.0
         roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None, "kernel": name,
+                "frac": ach / pk,
+                "traffic": captured_traffic(args.workload, args.precision, nrhs, name),
+                "kernel": name,
                 "peak_source": f"{peak_kind} bf16_tflops_sustained",
                 "note": "achieved counts 8 flops per complex MAC; the kernel executes "
                         + ("48 bf16 flops per complex MAC (3-way split, 6 slice products, "
@@ -357,6 +382,10 @@ def run_native(args):
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
                 "peak_source": f"{peak_kind} hbm_gbs", "share": ms / tot_ms}
+    if roof.get("traffic") is not None:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this "
+                                  "kernel, one capture of this bench on the same kernel source "
+                                  "(profiles/oz_gather_residual_far_sphere_r2_L5.md)")
     # ---- end to end through the host-buffer C-ABI call
     Bh = torch.empty((nrhs, sol.N), dtype=torch.complex128, pin_memory=True)
     Bh.copy_(B)
