@@ -162,6 +162,13 @@ def max_over_ranks(ws, val, device):
     return float(t.item())
 
 
+def job_rate(ws, units_per_rank, t_local, device):
+    """Whole-job rate: every rank processed `units_per_rank` units; the job took
+    the slowest rank's time.  Returns (time per step of the job, units/s)."""
+    t = max_over_ranks(ws, t_local, device)
+    return t, ws * units_per_rank / t
+
+
 def gemm_peak(dev, dtype):
     """ALU denominators: cuBLAS GEMM 4096^3 in the given dtype, best of 5 (TFLOP/s)."""
     import torch
@@ -324,8 +331,7 @@ def run_native(args):
     timed_launches = sol.stats()["kernel_launches"] - l0
     barrier(ws)
     t_dev = e0.elapsed_time(e1) / 1e3 / args.steps
-    t_dev = max_over_ranks(ws, t_dev, dev)
-    value = ws * nrhs / t_dev
+    t_dev, value = job_rate(ws, nrhs, t_dev, dev)
     ratio, _ = sol.diagnostics(nrhs)
     # ---- per-kernel timing (same steps, events around every launch)
     sol.profile_enable(True)
@@ -397,8 +403,8 @@ def run_native(args):
     for _ in range(args.steps):
         sol.solve_host(xn, bn)
     t_e2e = (time.perf_counter() - t0) / args.steps
-    t_e2e = max_over_ranks(ws, t_e2e, dev)
-    e2e = {"value": ws * nrhs / t_e2e, "unit": "RHS/s",
+    t_e2e, v_e2e = job_rate(ws, nrhs, t_e2e, dev)
+    e2e = {"value": v_e2e, "unit": "RHS/s",
            "h2d_bytes_per_step": int(bn.nbytes), "d2h_bytes_per_step": int(xn.nbytes)}
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws,
@@ -540,8 +546,7 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
-    t_dev = max_over_ranks(ws, e0.elapsed_time(e1) / 1e3 / args.steps, dev)
-    value = ws * nrhs_tot / t_dev
+    t_dev, value = job_rate(ws, nrhs_tot, e0.elapsed_time(e1) / 1e3 / args.steps, dev)
     # the same solves one after another on one stream (no graph)
     Ys = [torch.empty_like(B) for B in Bs]
     l0 = sols[0].stats()["kernel_launches"]
@@ -555,7 +560,7 @@ def run_batch(args):
             s.solve(Y, B)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_seq = e0.elapsed_time(e1) / 1e3 / args.steps
+    t_seq, v_seq = job_rate(ws, nrhs_tot, e0.elapsed_time(e1) / 1e3 / args.steps, dev)
     same = all(torch.equal(X, Y) for X, Y in zip(Xs, Ys))
     ratio_max = max(float(np.max(s.diagnostics(B.shape[0])[0])) for s, B in zip(sols, Bs))
     # per-kernel timing: one profiled pass of the single solves (events around
@@ -607,7 +612,7 @@ def run_batch(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    t_e2e = max_over_ranks(ws, (time.perf_counter() - t0) / args.steps, dev)
+    t_e2e, v_e2e = job_rate(ws, nrhs_tot, (time.perf_counter() - t0) / args.steps, dev)
     nbytes = sum(B.numel() * 16 for B in Bs)
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws,
@@ -627,12 +632,12 @@ def run_batch(args):
                    "device_gb_held_by_handles_before_first_solve": round(held_gb, 1),
                    "device_gb_free_before_first_solve": round(free_b / 1e9, 1)},
         "roofline": roof,
-        "e2e": {"value": ws * nrhs_tot / t_e2e, "unit": "RHS/s",
+        "e2e": {"value": v_e2e, "unit": "RHS/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches_per_step * args.steps,
         "graph_launches": args.steps,
         "clocks": clk.summary(),
-        "sequential": {"value": ws * nrhs_tot / t_seq, "unit": "RHS/s",
+        "sequential": {"value": v_seq, "unit": "RHS/s",
                        "ms_per_step": 1e3 * t_seq,
                        "what": "the same solves issued one after another, no graph",
                        "grouped_equals_sequential": same},
