@@ -162,6 +162,29 @@ def max_over_ranks(ws, val, device):
     return float(t.item())
 
 
+def workload_desc(w, N, nrhs):
+    """The workload named by both arms' config: mesh, size, tree, ACA and the
+    incidence sweep of a single-scatterer workload."""
+    lam = w.wavelength
+    kind = w.mesh[0]
+    if kind == "icosphere":
+        geo = f"PEC sphere r={w.mesh[2] / lam:g} lambda, icosphere L{w.mesh[1]}"
+    elif kind == "plate":
+        geo = f"PEC plate {w.mesh[1] / lam:g} x {w.mesh[1] / lam:g} lambda, " \
+              f"{w.mesh[2]} x {w.mesh[2]} cells"
+    else:
+        geo = f"PEC {kind} {w.mesh[1:]}"
+    sw = w.sweep
+    if sw[0] == "single":
+        rhs = f"{nrhs} RHS"
+    else:
+        pols = "/".join("theta" if p == 0 else "phi" for p in sw[5])
+        rhs = (f"{nrhs} monostatic RHS ({sw[0]} {sw[1]:g}..{sw[2]:g} step {sw[3]:g}, "
+               f"{pols} pol)")
+    aca = f"{w.aca_tol:.0e}".replace("e-0", "e-")
+    return f"{w.name}: {geo}, N={N}, leaves<={w.leaf_max}, ACA {aca}, {rhs}"
+
+
 def job_rate(ws, units_per_rank, t_local, device):
     """Whole-job rate: every rank processed `units_per_rank` units; the job took
     the slowest rank's time.  Returns (time per step of the job, units/s)."""
@@ -267,8 +290,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": f"{w.name}: PEC sphere r=2 lambda, icosphere L5, "
-                               f"N={H.N}, leaves<=128, ACA 1e-4, 362 monostatic RHS",
+        "config": {"workload": workload_desc(w, H.N, B.shape[1]),
                    "sample": f"{n} of {B.shape[1]} RHS per step"},
         "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": cpu_threads(), "kind": "oracle",
                          "sample": f"{n} RHS per step of the 362-RHS sweep, oracle set-up "
@@ -414,9 +436,7 @@ def run_native(args):
                  "mixed: c64 chain on tcgen05 (3-way bf16 split, f32 accum), c128 D^-1, "
                  "FP64-accurate residual on tcgen05 (exact 7-bit slicing)",
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: PEC sphere r=2 lambda, icosphere L5, N={sol.N}, "
-                               f"leaves<=128, ACA 1e-4, {nrhs} monostatic RHS "
-                               "(theta 0..180 step 1, theta/phi pol)",
+        "config": {"workload": workload_desc(w, sol.N, nrhs),
                    "precision": args.precision, "ordering": args.ordering,
                    "l2": "inputs larger than L2 (alpha + far factors), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU",

@@ -60,3 +60,11 @@ def test_captured_traffic_gated_on_source(monkeypatch):
     # a changed kernel source turns the figure off
     monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCE", (bench.NCU_TRAFFIC_SOURCE[0], "0" * 64))
     assert bench.captured_traffic(*key) is None
+
+
+def test_workload_description_of_the_benchmark():
+    # both arms (native and the oracle's) name the workload with this string
+    from hm_workloads import get_workload
+    assert bench.workload_desc(get_workload("sphere_r2_L5"), 30720, 362) == (
+        "sphere_r2_L5: PEC sphere r=2 lambda, icosphere L5, N=30720, leaves<=128, ACA 1e-4, "
+        "362 monostatic RHS (theta 0..180 step 1, theta/phi pol)")
