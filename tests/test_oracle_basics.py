@@ -130,6 +130,20 @@ def test_rwg_charge_neutral_and_normal_continuity():
             assert np.sign(flux) == sgn
 
 
+def far_pairs_separated(T, far):
+    """Every far pair's cells (boxes from the octree cube) leave a gap of at
+    least the smaller cell's edge on some axis (non-touching admissibility)."""
+    for s, t in far:
+        a, b = T.nodes[s], T.nodes[t]
+        ca, cb = T.size / 2 ** a.level, T.size / 2 ** b.level
+        lo_a = T.origin + np.array(a.ijk) * ca
+        lo_b = T.origin + np.array(b.ijk) * cb
+        gap = np.maximum(lo_b - (lo_a + ca), lo_a - (lo_b + cb))
+        if not gap.max() >= min(ca, cb) * (1 - 1e-9):
+            return False
+    return True
+
+
 def test_octree_tiling_and_admissibility():
     v, f = icosphere(3, 0.5)
     r = build_rwg(v, f)
@@ -144,8 +158,11 @@ def test_octree_tiling_and_admissibility():
     for s, t in far:
         a, b = T.nodes[s], T.nodes[t]
         cover[a.start:a.start + a.count, b.start:b.start + b.count] += 1
-        # separated cells: gap of at least one finest cell on some axis
         assert not T.touching(s, t)
+    # admissibility checked independently of touching(): the cell boxes of a
+    # far pair, from the cube's origin and size, are apart on some axis by at
+    # least the smaller cell, so the point sets are separated too
+    assert far_pairs_separated(T, far)
     assert cover.min() == 1 and cover.max() == 1
     assert sorted(T.perm.tolist()) == list(range(N))
     assert m.max() <= 64
