@@ -215,6 +215,61 @@ def pin_series(se):
                 np.all(relative_residual(H, B, xr) < relative_residual(H, B, x2)))
 
 
+def pin_rwg(rw):
+    """Interior-edge count 3F/2 on a closed mesh; the flux of every basis
+    function through its edge is l from T+ and -l into T- (normal continuity)."""
+    from hm_workloads import icosphere
+    v, f = icosphere(2, 0.5)
+    r = rw.build_rwg(v, f)
+    if r.n != 3 * len(f) // 2:
+        return False
+    for n in range(0, r.n, 7):
+        a, b = r.edge[n]
+        for tri, free, sgn in ((r.tri_p[n], r.free_p[n], 1.0), (r.tri_m[n], r.free_m[n], -1.0)):
+            vf = v[f[tri, free]]
+            mid = 0.5 * (v[a] + v[b])
+            fval = sgn * r.length[n] / (2 * r.area[tri]) * (mid - vf)
+            e = v[b] - v[a]
+            nrm = np.cross(v[f[tri, 1]] - v[f[tri, 0]], v[f[tri, 2]] - v[f[tri, 0]])
+            u = np.cross(e, nrm)
+            u /= np.linalg.norm(u)
+            if np.dot(u, mid - vf) < 0:
+                u = -u
+            flux = np.dot(fval, u) * np.linalg.norm(e)
+            if not (abs(abs(flux) - np.linalg.norm(e)) < 1e-12 and np.sign(flux) == sgn):
+                return False
+    return True
+
+
+def pin_hmatrix(hm):
+    """The assembled H-matrix is symmetric and within 3 eps of the EFIE
+    entries (0.5 lambda sphere); its products agree with the assembled matrix
+    through the many-terms series (LU limit) and the refinement residual."""
+    from tests.oracle_cases import case
+    from oracle.series import series_solve, refine_once, rel_err, relative_residual
+    rebuild = lambda H0: hm.HMatrix(N=H0.N, perm=H0.perm, leaf_off=H0.leaf_off,
+                                    near=H0.near, far=H0.far, k=H0.k, meta=H0.meta)
+    _, Zd, _ = dense_sphere_c1()[1:]
+    H1 = rebuild(case("sphere_r0.5_L3")[1])
+    Zh = H1.to_dense()
+    Zp = Zd[np.ix_(H1.perm, H1.perm)]
+    if not (np.array_equal(Zh, Zh.T) and
+            np.linalg.norm(Zh - Zp) / np.linalg.norm(Zp) < 3e-4):
+        return False
+    H0, S, B = plate_converging()
+    H = rebuild(H0)
+    x_lu = np.linalg.solve(H.to_dense(), B[H.perm])
+    X = np.empty_like(x_lu)
+    X[H.perm] = x_lu
+    with np.errstate(all="ignore"):
+        x40, _ = series_solve(H, S, B, 40)
+        x2, _ = series_solve(H, S, B, 2)
+        xr = refine_once(H, S, B, x2)
+    return bool(np.all(rel_err(x40, X) < 1e-10) and
+                np.all(rel_err(xr, X) < rel_err(x2, X)) and
+                np.all(relative_residual(H, B, xr) < relative_residual(H, B, x2)))
+
+
 # -------------------------------------------------------------- the mutants
 MUTANTS = [
     # (id, module, pin, original text, planted mistake)
@@ -239,6 +294,18 @@ MUTANTS = [
      "xi = x * (jn + 1j * yn)", "xi = x * (jn - 1j * yn)"),
     ("octree_touching_off_by_one", "octree", pin_octree,
      "if lo_a > hi_b or lo_b > hi_a:", "if lo_a >= hi_b or lo_b >= hi_a:"),
+    ("rwg_edge_opposite_wrong_vertex", "rwg", pin_rwg,
+     "a, b = int(tv[(k + 1) % 3]), int(tv[(k + 2) % 3])",
+     "a, b = int(tv[k]), int(tv[(k + 1) % 3])"),
+    ("rwg_area_without_half", "rwg", pin_rwg,
+     "area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)",
+     "area = np.linalg.norm(np.cross(b - a, c - a), axis=1)"),
+    ("far_product_conjugated_lower_block", "hmatrix", pin_hmatrix,
+     "y[cs] += Q @ (P.T @ x[rs])", "y[cs] += Q.conj() @ (P.conj().T @ x[rs])"),
+    ("near_product_conjugated_lower_block", "hmatrix", pin_hmatrix,
+     "y[sj] += Bk.T @ x[si]", "y[sj] += Bk.conj().T @ x[si]"),
+    ("assembled_lower_far_block_hermitian", "hmatrix", pin_hmatrix,
+     "Z[c0:c0 + n, r0:r0 + m] = Bk.T", "Z[c0:c0 + n, r0:r0 + m] = Bk.conj().T"),
     ("aca_residual_sign", "aca", pin_aca,
      "row -= u[i] * v", "row += u[i] * v"),
     ("recompress_conjugate", "aca", pin_aca,
@@ -270,7 +337,7 @@ MUTANTS = [
                          ids=lambda v: getattr(v, "__name__", v))
 def test_pins_accept_the_oracle(pin, modname):
     if pin is pin_efie:
-        assert pin(None)
+        assert pin(None)                 # the filled Z of the committed EFIE
     else:
         assert pin(load(modname))
 
