@@ -239,19 +239,63 @@ def oracle_time(H, S, B, nrhs_sample, reps):
     return len(idx), ts
 
 
+def openblas_threads():
+    """(set, get) thread-count functions of the OpenBLAS that NumPy loaded
+    (found by name among the process's mapped libraries), or None."""
+    import ctypes
+    try:
+        with open("/proc/self/maps") as f:
+            paths = sorted({ln.split()[-1] for ln in f
+                            if "openblas" in ln.lower() and ".so" in ln})
+    except OSError:
+        return None
+    for path in paths:
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for pre, suf in (("scipy_openblas", "64_"), ("openblas", ""), ("openblas", "64_"),
+                         ("scipy_openblas", "")):
+            st, gt = f"{pre}_set_num_threads{suf}", f"{pre}_get_num_threads{suf}"
+            if hasattr(lib, st) and hasattr(lib, gt):
+                return getattr(lib, st), getattr(lib, gt)
+    return None
+
+
 def oracle_job(name, processes, nrhs_sample, reps, conn):
-    """Oracle set-up and timed sample in a separate (spawned) process; the
-    result goes back through a pipe."""
+    """Oracle set-up and timed sample in a separate (spawned) process, with
+    NumPy's BLAS on all its threads and then on one; the result goes back
+    through a pipe."""
     try:
         from hm_workloads import get_workload
         w = get_workload(name)
         H, S, B, setup_s = oracle_setup(w, processes)
         n, ts = oracle_time(H, S, B, nrhs_sample, reps)
-        conn.send({"n": n, "ts": ts, "setup_s": setup_s, "threads": cpu_threads(),
-                   "nrhs": B.shape[1]})
+        threads, one = cpu_threads(), None
+        ob = openblas_threads()
+        if ob is not None:
+            set_t, get_t = ob
+            threads = int(get_t())
+            set_t(1)
+            try:
+                n1, ts1 = oracle_time(H, S, B, nrhs_sample, 1)
+            finally:
+                set_t(threads)
+            one = {"n": n1, "ts": ts1}
+        conn.send({"n": n, "ts": ts, "setup_s": setup_s, "threads": threads,
+                   "nrhs": B.shape[1], "one_thread": one})
     except Exception as e:  # reported in the JSON line
         conn.send({"error": repr(e)})
     conn.close()
+
+
+def one_thread_entry(res):
+    """The oracle's rate with NumPy's BLAS on one thread, for cpu_baseline."""
+    one = res.get("one_thread")
+    if not one:
+        return {"value": None, "note": "OpenBLAS thread control not found"}
+    return {"value": one["n"] / min(one["ts"]), "unit": "RHS/s", "cores": 1,
+            "sample": f"the same {one['n']} RHS, one run"}
 
 
 def start_oracle(name, nrhs_sample, reps):
@@ -285,6 +329,16 @@ def run_reference(args):
     ts = ts[args.warmup:]
     t = sum(ts) / len(ts)
     val = n / t
+    threads, one = cpu_threads(), {"one_thread": None}
+    ob = openblas_threads()
+    if ob is not None:
+        threads = int(ob[1]())
+        ob[0](1)
+        try:
+            n1, ts1 = oracle_time(H, S, B, args.cpu_rhs, 1)
+        finally:
+            ob[0](threads)
+        one = {"one_thread": {"n": n1, "ts": ts1}}
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "RHS/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -292,9 +346,10 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": workload_desc(w, H.N, B.shape[1]),
                    "sample": f"{n} of {B.shape[1]} RHS per step"},
-        "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{n} RHS per step of the 362-RHS sweep, oracle set-up "
-                                   f"{setup_s:.0f} s (not timed, {procs} processes)"},
+        "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{n} RHS per step of the {B.shape[1]}-RHS sweep, oracle "
+                                   f"set-up {setup_s:.0f} s (not timed, {procs} processes)",
+                         "single_thread": one_thread_entry(one)},
         "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -498,7 +553,8 @@ def run_native(args):
                 "sample": f"{res['n']} of {res['nrhs']} RHS of the same sweep, oracle FP64 "
                           f"series solve (NumPy), best of 2; oracle set-up "
                           f"{res['setup_s']:.0f} s untimed ({procs} processes, during the GPU "
-                          "measurement)"}
+                          "measurement)",
+                "single_thread": one_thread_entry(res)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -677,7 +733,8 @@ def run_batch(args):
                 "kind": "oracle",
                 "sample": f"{res['n']} of {res['nrhs']} RHS of the smallest scatterer "
                           f"({ws_list[small].name}, N={Ns[small]}), oracle FP64 series "
-                          f"solve (NumPy), best of 2"}
+                          f"solve (NumPy), best of 2",
+                "single_thread": one_thread_entry(res)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -68,3 +68,22 @@ def test_workload_description_of_the_benchmark():
     assert bench.workload_desc(get_workload("sphere_r2_L5"), 30720, 362) == (
         "sphere_r2_L5: PEC sphere r=2 lambda, icosphere L5, N=30720, leaves<=128, ACA 1e-4, "
         "362 monostatic RHS (theta 0..180 step 1, theta/phi pol)")
+
+
+def test_openblas_thread_control_and_single_thread_entry():
+    import numpy as np
+    a = np.ones((64, 64))
+    a @ a                                          # BLAS loaded and initialised
+    ob = bench.openblas_threads()
+    if ob is not None:                             # NumPy built on OpenBLAS
+        set_t, get_t = ob
+        n = int(get_t())
+        set_t(1)
+        try:
+            assert int(get_t()) == 1
+        finally:
+            set_t(n)
+        assert int(get_t()) == n
+    e = bench.one_thread_entry({"one_thread": {"n": 4, "ts": [2.0, 1.0]}})
+    assert e["value"] == 4.0 and e["cores"] == 1
+    assert bench.one_thread_entry({"one_thread": None})["value"] is None
