@@ -346,3 +346,58 @@ def test_pins_accept_the_oracle(pin, modname):
 def test_pins_reject_planted_mistake(case):
     _, modname, pin, old, new = case
     assert not pin(load(modname, old, new))
+
+
+# ------------------------------------------- the plain-C entry (oracle/cefie.c)
+def pin_cefie(cm):
+    """The C entry equals the NumPy EFIE entry (relative 1e-12) on self,
+    touching and separated pairs of a small sphere."""
+    from hm_workloads import icosphere
+    from oracle.efie import EFIE
+    from oracle.rwg import build_rwg
+    v, f = icosphere(2, 0.5)
+    r = build_rwg(v, f)
+    E = EFIE(r)
+    rows, cols = np.arange(0, r.n, 7), np.arange(r.n)
+    a = E.block(rows, cols)
+    return bool(np.abs(a - cm.CBlock(E)(rows, cols)).max() < 1e-12 * np.abs(a).max())
+
+
+C_MUTANTS = [
+    ("green_phase_sign", "gi = -s * inv4pi / R;", "gi = s * inv4pi / R;"),
+    ("singular_part_not_subtracted", "gr = (touch ? c - 1.0 : c) * inv4pi / R;",
+     "gr = c * inv4pi / R;"),
+    ("solid_angle_dropped", "*Is += t * f - ah * beta;", "*Is += t * f;"),
+    ("scalar_potential_sign", "((M->k / 4.0) * A - S[0][c] / M->k)",
+     "((M->k / 4.0) * A + S[0][c] / M->k)"),
+]
+
+
+def load_c(tmp_path, old=None, new=None):
+    """oracle.cefie bound to a copy of cefie.c (with `old` replaced by `new`)
+    compiled into tmp_path."""
+    import subprocess
+    with open(os.path.join(ORACLE_DIR, "cefie.c")) as f:
+        src = f.read()
+    if old is not None:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    c = tmp_path / "cefie.c"
+    so = tmp_path / "cefie.so"
+    c.write_text(src)
+    subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-ffp-contract=off",
+                           "-o", str(so), str(c), "-lm"])
+    mod = load("cefie")
+    mod._SRC, mod._LIB = str(c), None
+    mod.lib_path = lambda: str(so)
+    return mod
+
+
+def test_c_pin_accepts_the_oracle(tmp_path):
+    assert pin_cefie(load_c(tmp_path))
+
+
+@pytest.mark.parametrize("case", C_MUTANTS, ids=[m[0] for m in C_MUTANTS])
+def test_c_pin_rejects_planted_mistake(case, tmp_path):
+    _, old, new = case
+    assert not pin_cefie(load_c(tmp_path, old, new))
