@@ -58,3 +58,18 @@ def test_null_arguments_rejected(lib):
     nr = (ctypes.c_int * 1)(1)
     assert lib.hm_solve_grouped(arr, arr, arr, nr, 1) == hp.HM_ERR_INVALID
     assert lib.hm_solve_grouped(arr, arr, arr, nr, 0) == hp.HM_ERR_INVALID
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    """A copy of the binding with no libhmps.so beside it refuses to import:
+    there is no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "hmps_copy"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2109_04129_gb300", "__init__.py"), pkg / "__init__.py")
+    r = subprocess.run([sys.executable, "-c", "import hmps_copy"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "native library not built" in r.stderr
