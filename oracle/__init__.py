@@ -20,6 +20,9 @@ Modules, in the order the method uses them:
   series       two-term (or n-term) power series            (Eq. 30-45)
   rcs          radiation integral, RCS, Mie series           (Sec. V)
   export       writer of the neutral block file the GPU library imports
+  cefie        plain-C statement of the EFIE entry (fast fills for large meshes)
+  study_leaf_size  series accuracy against the leaf size  (Sec. V-A, Fig. 4);
+               a study run from the command line, not a step of the method
 
 Parity status of every function is listed in its module docstring; functions
 without an independent pin say "parity unpinned".
