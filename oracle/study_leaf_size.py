@@ -11,6 +11,7 @@ first cap's matrix for all caps (`--ref first`, one LU for large N; the
 matrices differ only by the ACA tolerance).
 
     python -m oracle.study_leaf_size --level 4 --radius 1.0 --caps 32 64 128 256 512 1024
+    python -m oracle.study_leaf_size --level 4 --radius 1.0 --caps 64 256 --eta 1
 
 prints one line per cap: leaves, leaf cell edge in wavelengths (min / median
 / max over the leaves), the Eq. 45 ratio ||it_1|| / ||it_0||, and the errors.
@@ -19,6 +20,28 @@ import argparse
 import time
 
 import numpy as np
+
+
+def eta_octree(eta):
+    """Octree whose admissibility is the paper's form with constant eta
+    (Eq. 10): cells s, t are far when min(diam_s, diam_t) <= eta dist(s, t),
+    diam the cell diagonal and dist the distance between the cells, and
+    never when they touch.  For the study only; the oracle and the GPU
+    library use non-touching admissibility."""
+    import math
+    from .octree import Octree
+
+    class EtaOctree(Octree):
+        def touching(self, s, t):          # True = not admissible (near)
+            a, b = self.nodes[s], self.nodes[t]
+            ca, cb = self.size / 2 ** a.level, self.size / 2 ** b.level
+            lo_a = self.origin + np.array(a.ijk) * ca
+            lo_b = self.origin + np.array(b.ijk) * cb
+            gap = np.maximum(0.0, np.maximum(lo_b - (lo_a + ca), lo_a - (lo_b + cb)))
+            dist = float(np.linalg.norm(gap))
+            return not (dist > 0.0 and math.sqrt(3.0) * min(ca, cb) <= eta * dist)
+
+    return EtaOctree
 
 
 def leaf_edges(tree, wavelength):
@@ -39,11 +62,18 @@ def main():
     ap.add_argument("--terms", type=int, nargs="+", default=[2, 3, 5])
     ap.add_argument("--ref", choices=["own", "first"], default="own")
     ap.add_argument("--processes", type=int, default=None)
+    ap.add_argument("--eta", type=float, default=None,
+                    help="admissibility min(diam) <= eta dist instead of non-touching cells")
     a = ap.parse_args()
+    if a.eta is not None:
+        from . import hmatrix
+        hmatrix.Octree = eta_octree(a.eta)
     v, f = icosphere(a.level, a.radius)
     procs = a.processes or default_processes()
     ref = None
-    print(f"# icosphere L{a.level}, radius {a.radius} lambda, reference LU ({a.ref})", flush=True)
+    adm = f"eta {a.eta:g}" if a.eta is not None else "non-touching"
+    print(f"# icosphere L{a.level}, radius {a.radius} lambda, admissibility {adm}, "
+          f"reference LU ({a.ref})", flush=True)
     print("# cap leaves edge_min edge_med edge_max ratio_eq45 "
           + " ".join(f"err_{t}" for t in a.terms) + " seconds", flush=True)
     for cap in a.caps:

@@ -20,3 +20,30 @@ def test_leaf_size_study_runs():
     assert int(small[1]) > int(one_leaf[1]) == 1
     # a single leaf: no far field, the series is exact
     assert float(one_leaf[6]) < 1e-10 and float(one_leaf[7]) < 1e-10
+
+
+def test_eta_admissibility_reduces_to_non_touching():
+    """Non-touching cells are at least one smaller-cell edge apart, so the
+    paper-form admissibility min(diam) <= eta dist with eta >= sqrt(3) gives
+    the same block tree; a stricter eta only moves pairs from far to near."""
+    import math
+    import numpy as np
+    from hm_workloads import icosphere
+    from oracle.octree import Octree
+    from oracle.rwg import build_rwg
+    from oracle.study_leaf_size import eta_octree
+    v, f = icosphere(3, 0.5)
+    pts = build_rwg(v, f).centre
+    near0, far0 = Octree(pts, 32).blocks()
+    near1, far1 = eta_octree(math.sqrt(3.0) * (1 + 1e-12))(pts, 32).blocks()
+    assert sorted(near0) == sorted(near1) and sorted(far0) == sorted(far1)
+    T = eta_octree(1.0)(pts, 32)
+    near2, far2 = T.blocks()
+    assert set(near0) < set(near2)
+    cover = np.zeros((len(pts), len(pts)), np.int8)
+    for i, j in near2:
+        cover[T.leaf_off[i]:T.leaf_off[i + 1], T.leaf_off[j]:T.leaf_off[j + 1]] += 1
+    for s, t in far2:
+        a, b = T.nodes[s], T.nodes[t]
+        cover[a.start:a.start + a.count, b.start:b.start + b.count] += 1
+    assert cover.min() == 1 and cover.max() == 1
