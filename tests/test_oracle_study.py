@@ -47,3 +47,20 @@ def test_eta_admissibility_reduces_to_non_touching():
         a, b = T.nodes[s], T.nodes[t]
         cover[a.start:a.start + a.count, b.start:b.start + b.count] += 1
     assert cover.min() == 1 and cover.max() == 1
+
+
+def test_fill_study_counts_equal_the_scaling():
+    """The symbolic counts of the memory study equal the entries of the
+    numerical scaling (readings A in both orders, B) and of the near field."""
+    from oracle.scaling import compute_scaling, nd_order
+    from oracle.study_fill import counts
+    from tests.oracle_cases import case
+    _, H, SA, _ = case("sphere_r0.5_L3")
+    N, nl, zn, d, ad, an, ab = counts(H.rwg.centre, H.meta["leaf_max"])
+    assert (N, nl) == (H.N, H.n_leaves)
+    assert zn == sum(b.size for b in H.near.values())
+    assert (ad, d) == SA.entries(H.leaf_off)
+    SN = compute_scaling(H, "A", nd_order(H.tree, list(H.near.keys())))
+    assert an == SN.entries(H.leaf_off)[0]
+    assert ab == compute_scaling(H, "B").entries(H.leaf_off)[0]
+    assert ab < zn < ad                     # reading B below the near field, A above
