@@ -21,9 +21,10 @@
 //     words into one (bits below 2^-49 of the row and column scales dropped),
 //     and that word is added to an FP64 accumulator with one fused
 //     multiply-add.
-// Dropped terms (L >= 8) and the truncated bits are below 2^-55 of the
-// row/column scales times the inner length, plus 2^-49 of the scales per
-// window: FP64-class accuracy.
+// Dropped terms (L >= 8) and the truncated bits are below 2^-52.5 of the
+// row/column scales per real product term (two per complex inner row), plus
+// 2^-49 of the scales per window and the FP64 rounding of each window's sum:
+// FP64-class accuracy.
 //
 // Complex products use the real-expanded block (rows [a_re, -a_im] and
 // [a_im, a_re] over interleaved inner k) as in the mixed-precision engine.

@@ -45,12 +45,11 @@ def test_job_rate_one_rank():
 
 
 def test_captured_traffic_gated_on_source(monkeypatch):
-    import hashlib
     key = ("sphere_r2_L5", "mixed", 362, "far_stage2")
     assert key in bench.NCU_TRAFFIC
-    # a source that hashes to the recorded value reports the captured figure
-    with open(os.path.join(ROOT, bench.NCU_TRAFFIC_SOURCE[0]), "rb") as f:
-        now = hashlib.sha256(f.read()).hexdigest()
+    # a source whose code hashes to the recorded value reports the captured figure
+    with open(os.path.join(ROOT, bench.NCU_TRAFFIC_SOURCE[0])) as f:
+        now = bench.code_hash(f.read())
     monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCE", (bench.NCU_TRAFFIC_SOURCE[0], now))
     assert bench.captured_traffic(*key) == bench.NCU_TRAFFIC[key]
     # not captured: other kernel, precision or RHS count
@@ -87,3 +86,9 @@ def test_openblas_thread_control_and_single_thread_entry():
     e = bench.one_thread_entry({"one_thread": {"n": 4, "ts": [2.0, 1.0]}})
     assert e["value"] == 4.0 and e["cores"] == 1
     assert bench.one_thread_entry({"one_thread": None})["value"] is None
+
+
+def test_code_hash_ignores_comments_only():
+    src = "int f(int a) {  // add one\n  return a + 1; /* done */ }\n"
+    assert bench.code_hash(src) == bench.code_hash("int f(int a) { return a + 1; }")
+    assert bench.code_hash(src) != bench.code_hash("int f(int a) { return a + 2; }")
