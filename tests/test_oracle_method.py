@@ -217,3 +217,17 @@ def test_nested_dissection_order_same_solution():
     M = R.T @ ZN @ R
     for k, sk in enumerate(S2.slices(H.leaf_off)):
         assert np.allclose(M[sk, sk], S2.D[k], atol=1e-11 * np.abs(M).max())
+
+
+def test_phi_polarised_wave_matches_mie_h_plane():
+    """The phi-polarised wave from theta = 0, phi = 0 is y-polarised, so the
+    xz-plane is its H-plane: the phi component of the bistatic RCS there
+    follows the Mie series' S1 pattern (0.5 dB)."""
+    r, E, Zd, _ = dense_sphere_c1()
+    b = E.plane_wave([0.0], [0.0], [1])
+    x = np.linalg.solve(Zd, b)
+    th = np.radians(np.arange(0.0, 181.0, 5.0))
+    s = rcs(r, E.k, x, th, 0.0, "phi")[:, 0]
+    m = mie_bistatic(0.5, E.k, np.pi - th, "H")
+    db = 10 * np.log10(s / m)
+    assert np.abs(db).max() < 0.5, db

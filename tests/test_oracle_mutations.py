@@ -93,6 +93,17 @@ def pin_plane_wave(ef):
     return bool(np.abs(_mie_db(r, E0.k, np.linalg.solve(Zd, b))).max() < 0.5)
 
 
+def pin_phi_polarisation(ef):
+    """The phi-polarised wave from theta = 0 (y-polarised) against the Mie
+    series' H-plane pattern in the xz-plane."""
+    from oracle.rcs import rcs, mie_bistatic
+    r, E0, Zd, _ = dense_sphere_c1()
+    b = ef.EFIE(r, 1.0).plane_wave([0.0], [0.0], [1])
+    th = np.radians(np.arange(0.0, 181.0, 5.0))
+    s = rcs(r, E0.k, np.linalg.solve(Zd, b), th, 0.0, "phi")[:, 0]
+    return bool(np.abs(10 * np.log10(s / mie_bistatic(0.5, E0.k, np.pi - th, "H"))).max() < 0.5)
+
+
 def pin_rcs(rc):
     """Monostatic sweep RCS of the LU currents against the Mie series."""
     r, E0, Zd, B = dense_sphere_c1()
@@ -288,6 +299,9 @@ MUTANTS = [
     ("plane_wave_direction", "efie", pin_plane_wave,
      "khat = -np.stack([st * cp, st * sp, ct], axis=1)",
      "khat = np.stack([st * cp, st * sp, ct], axis=1)"),
+    ("phi_polarisation_uses_theta_hat", "efie", pin_phi_polarisation,
+     "phat = np.where((pol == 0)[:, None], th_hat, ph_hat)",
+     "phat = np.where((pol == 0)[:, None], th_hat, th_hat)"),
     ("rcs_constant", "rcs", pin_rcs,
      "(k * k * ETA0 * ETA0 / (4 * math.pi))", "(k * k * ETA0 * ETA0 / (2 * math.pi))"),
     ("mie_hankel_kind", "rcs", pin_mie,
