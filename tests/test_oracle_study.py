@@ -1,9 +1,11 @@
-"""The leaf-size study script (Sec. V-A, Fig. 4) runs on a tiny sphere: one
-line per leaf cap, and where every leaf pair is near (Z_F = 0) the series
-equals the LU solution."""
+"""The oracle's study scripts on small cases: the leaf-size study (Sec. V-A,
+Fig. 4) and its admissibility option, the memory study's counts against the
+numerical scaling, and the mixed-precision error model."""
 import os
 import subprocess
 import sys
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -64,3 +66,18 @@ def test_fill_study_counts_equal_the_scaling():
     assert an == SN.entries(H.leaf_off)[0]
     assert ab == compute_scaling(H, "B").entries(H.leaf_off)[0]
     assert ab < zn < ad                     # reading B below the near field, A above
+
+
+def test_mixed_error_model_small_case():
+    """The mixed-precision model runs on a small case: the chain's complex64
+    storage alone moves the refined solution by FP32-level amounts, complex64
+    arithmetic by more, both far below the mixed bar of 1e-4."""
+    from oracle.series import rel_err
+    from oracle.study_mixed_error import mixed_model
+    from tests.oracle_cases import case
+    _, H, S, B = case("sphere_r0.25_L2")
+    xs, x64 = mixed_model(H, S, B[:, :4], arithmetic=False)
+    xa, _ = mixed_model(H, S, B[:, :4], arithmetic=True)
+    es, ea = rel_err(xs, x64), rel_err(xa, x64)
+    assert np.all(es > 0) and np.all(es < 1e-5)
+    assert np.all(ea < 1e-4) and ea.max() > es.max()
