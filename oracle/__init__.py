@@ -21,8 +21,11 @@ Modules, in the order the method uses them:
   rcs          radiation integral, RCS, Mie series           (Sec. V)
   export       writer of the neutral block file the GPU library imports
   cefie        plain-C statement of the EFIE entry (fast fills for large meshes)
-  study_leaf_size  series accuracy against the leaf size  (Sec. V-A, Fig. 4);
-               a study run from the command line, not a step of the method
+  study_leaf_size  series accuracy against the leaf size  (Sec. V-A, Fig. 4)
+  study_fill       near-field and scaling-coefficient memory against N
+  study_mixed_error  precision model of the mixed path (not in the paper)
+               (the three studies run from the command line; they are not
+               steps of the method)
 
 Parity status of every function is listed in its module docstring; functions
 without an independent pin say "parity unpinned".
