@@ -73,6 +73,8 @@ def parse():
                     help="skip the plain FP64 GPU solve measured beside the mixed one")
     ap.add_argument("--ordering", default="nd", choices=["nd", "dfs"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-single-rhs", action="store_true",
+                    help="skip the one-RHS (bandwidth-bound) leg")
     ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="scatterers in --workload scatterer_batch")
@@ -236,15 +238,20 @@ def oracle_setup(w, processes):
     return H, S, B, time.perf_counter() - t0
 
 
-def oracle_time(H, S, B, nrhs_sample, reps):
-    """Oracle series solve (plain NumPy FP64) of a bounded RHS sample."""
-    from oracle.series import series_solve
+def oracle_time(H, S, B, nrhs_sample, reps, refine=True):
+    """Oracle solve (plain NumPy FP64) of a bounded RHS sample, timed per
+    repetition.  refine=True times the work of the mixed path: the two-term
+    series, the FP64 residual and the series of the refinement step
+    (oracle.series.refine_once); refine=False the plain two-term series."""
+    from oracle.series import refine_once, series_solve
     idx = list(range(0, B.shape[1], max(1, B.shape[1] // nrhs_sample)))[:nrhs_sample]
     Bs = B[:, idx]
     ts = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        series_solve(H, S, Bs, 2)
+        x2, _ = series_solve(H, S, Bs, 2)
+        if refine:
+            refine_once(H, S, Bs, x2)
         ts.append(time.perf_counter() - t0)
     return len(idx), ts
 
@@ -273,14 +280,21 @@ def openblas_threads():
 
 
 def oracle_job(name, processes, nrhs_sample, reps, conn):
-    """Oracle set-up and timed sample in a separate (spawned) process, with
-    NumPy's BLAS on all its threads and then on one; the result goes back
-    through a pipe."""
+    """Oracle set-up, then (on "go") the timed sample, in a separate (spawned)
+    process: the series + refinement (like-for-like with the mixed GPU path)
+    and the plain series with NumPy's BLAS on all its threads, then the first
+    again with that BLAS on one thread.  It reports "ready" after the set-up
+    and waits for "go", which the GPU side sends after its own measurements,
+    so the two never run at the same time."""
     try:
         from hm_workloads import get_workload
         w = get_workload(name)
         H, S, B, setup_s = oracle_setup(w, processes)
-        n, ts = oracle_time(H, S, B, nrhs_sample, reps)
+        conn.send({"ready": True})
+        if conn.recv() != "go":
+            return
+        n, ts = oracle_time(H, S, B, nrhs_sample, reps, refine=True)
+        _, ts_plain = oracle_time(H, S, B, nrhs_sample, reps, refine=False)
         threads, one = cpu_threads(), None
         ob = openblas_threads()
         if ob is not None:
@@ -288,12 +302,12 @@ def oracle_job(name, processes, nrhs_sample, reps, conn):
             threads = int(get_t())
             set_t(1)
             try:
-                n1, ts1 = oracle_time(H, S, B, nrhs_sample, 1)
+                n1, ts1 = oracle_time(H, S, B, nrhs_sample, 1, refine=True)
             finally:
                 set_t(threads)
             one = {"n": n1, "ts": ts1}
-        conn.send({"n": n, "ts": ts, "setup_s": setup_s, "threads": threads,
-                   "nrhs": B.shape[1], "one_thread": one})
+        conn.send({"n": n, "ts": ts, "ts_plain": ts_plain, "setup_s": setup_s,
+                   "threads": threads, "nrhs": B.shape[1], "one_thread": one})
     except Exception as e:  # reported in the JSON line
         conn.send({"error": repr(e)})
     conn.close()
@@ -311,11 +325,44 @@ def one_thread_entry(res):
 def start_oracle(name, nrhs_sample, reps):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    parent, child = ctx.Pipe(duplex=False)
+    parent, child = ctx.Pipe(duplex=True)
     procs = max(1, min(16, (os.cpu_count() or 2) - 2))
     p = ctx.Process(target=oracle_job, args=(name, procs, nrhs_sample, reps, child))
     p.start()
-    return p, parent, procs
+    return {"proc": p, "conn": parent, "procs": procs, "error": None}
+
+
+def oracle_ready(oracle):
+    """Block until the oracle process has finished its set-up (before the GPU's
+    timed region, so that the set-up's worker processes do not share the host
+    with it)."""
+    if oracle is None:
+        return
+    msg = oracle["conn"].recv()
+    if "error" in msg:
+        oracle["error"] = msg
+
+
+def oracle_result(oracle, what):
+    """Send "go", collect the timed sample and format cpu_baseline."""
+    proc, conn, procs = oracle["proc"], oracle["conn"], oracle["procs"]
+    res = oracle["error"]
+    if res is None:
+        conn.send("go")
+        res = conn.recv()
+    proc.join()
+    if "error" in res:
+        return {"value": None, "unit": "RHS/s", "kind": "oracle", "error": res["error"]}
+    t = min(res["ts"])
+    return {"value": res["n"] / t, "unit": "RHS/s", "cores": res["threads"], "kind": "oracle",
+            "sample": f"{res['n']} of {res['nrhs']} RHS of {what}, oracle FP64 two-term series "
+                      f"+ one refinement step (residual and second series: the mixed path's "
+                      f"work), best of {len(res['ts'])}; oracle set-up {res['setup_s']:.0f} s "
+                      f"untimed ({procs} processes, finished before the GPU's timed region; "
+                      f"the sample ran after it)",
+            "series_only": {"value": res["n"] / min(res["ts_plain"]), "unit": "RHS/s",
+                            "what": "plain two-term series on the same sample"},
+            "single_thread": one_thread_entry(res)}
 
 
 def cpu_threads():
@@ -335,10 +382,12 @@ def run_reference(args):
     w = get_workload(args.workload)
     procs = max(1, min(16, os.cpu_count() or 1))
     H, S, B, setup_s = oracle_setup(w, procs)
-    n, ts = oracle_time(H, S, B, args.cpu_rhs, args.warmup + args.steps)
+    # one step = the mixed path's work on the sample: series + refinement
+    n, ts = oracle_time(H, S, B, args.cpu_rhs, args.warmup + args.steps, refine=True)
     ts = ts[args.warmup:]
     t = sum(ts) / len(ts)
     val = n / t
+    _, ts_plain = oracle_time(H, S, B, args.cpu_rhs, 1, refine=False)
     threads, one = cpu_threads(), {"one_thread": None}
     ob = openblas_threads()
     if ob is not None:
@@ -358,7 +407,11 @@ def run_reference(args):
                    "sample": f"{n} of {B.shape[1]} RHS per step"},
         "cpu_baseline": {"value": val, "unit": "RHS/s", "cores": threads, "kind": "oracle",
                          "sample": f"{n} RHS per step of the {B.shape[1]}-RHS sweep, oracle "
-                                   f"set-up {setup_s:.0f} s (not timed, {procs} processes)",
+                                   f"FP64 two-term series + one refinement step (the mixed "
+                                   f"path's work); oracle set-up {setup_s:.0f} s (not timed, "
+                                   f"{procs} processes)",
+                         "series_only": {"value": n / min(ts_plain), "unit": "RHS/s",
+                                         "what": "plain two-term series on the same sample"},
                          "single_thread": one_thread_entry(one)},
         "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -368,8 +421,9 @@ def run_reference(args):
 # ----------------------------------------------------------------- native leg
 def run_native(args):
     ws, rank, local = dist_setup(args)
-    # the oracle leg starts before the first GPU call (spawned, CPU only) and
-    # runs while the GPU is measured
+    # the oracle leg starts before the first GPU call (spawned, CPU only); its
+    # set-up overlaps the GPU set-up, and its timed sample runs after every
+    # GPU measurement (oracle_ready / oracle_result)
     oracle = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         oracle = start_oracle(args.workload, args.cpu_rhs, 2)
@@ -401,6 +455,7 @@ def run_native(args):
     for _ in range(args.warmup):
         sol.solve(X, B)
     torch.cuda.synchronize()
+    oracle_ready(oracle)
     # ---- timed region: device-resident inputs (alpha/far data > L2: no flush)
     barrier(ws)
     torch.cuda.synchronize()
@@ -427,58 +482,12 @@ def run_native(args):
     prof = sol.profile()
     sol.profile_enable(False)
     peaks, peak_kind = measured_peaks()
-    fp64_peak = gemm_peak(dev, torch.float64)
-    fp32_peak = gemm_peak(dev, torch.float32)
-    fp32_cats = {"mixed_sweep", "mixed_far"}
-    tensor_cats = {"mixed_sweep", "mixed_far"} if prec == hp.HM_MIXED else set()
-    oz_cats = {"far_stage1", "far_stage2", "near"} if prec == hp.HM_MIXED else set()
-    tot_ms = sum(p[1] for p in prof.values())
-    kernels = {}
-    for cat, (launches, ms, byts, flops) in prof.items():
-        if not launches:
-            continue
-        kernels[cat] = {"ms_per_step": round(ms / args.steps, 3), "share": round(ms / tot_ms, 4),
-                        "launches_per_step": int(launches / args.steps),
-                        "tflops": round(flops / (ms / 1e3) / 1e12, 4),
-                        "gbs": round(byts / (ms / 1e3) / 1e9, 2)}
-    name, (launches, ms, byts, flops) = max(prof.items(), key=lambda kv: kv[1][1])
-    avg_s = ms / 1e3 / max(1.0, launches)
-    if flops > 0 and (name in tensor_cats or name in oz_cats):
-        # bf16 tensor-core kernels: algorithmic complex-MAC flops (8 per MAC)
-        # against the measured dense bf16 peak (sustained: timed inside a long step)
-        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-        ach = flops / max(launches, 1) / avg_s / 1e12
-        # executed bf16 flops per algorithmic flop: 6 slice products (three-way
-        # split) or 36 digit products (FP64-accurate slicing)
-        xf = 6.0 if name in tensor_cats else 36.0
-        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk,
-                "traffic": captured_traffic(args.workload, args.precision, nrhs, name),
-                "kernel": name,
-                "peak_source": f"{peak_kind} bf16_tflops_sustained",
-                "note": "achieved counts 8 flops per complex MAC; the kernel executes "
-                        + ("48 bf16 flops per complex MAC (3-way split, 6 slice products, "
-                           "real-expanded complex)" if name in tensor_cats else
-                           "288 bf16 flops per complex MAC (8 digits, 36 slice products)"),
-                "executed_tflops": ach * xf, "executed_frac": ach * xf / pk,
-                "share": ms / tot_ms}
-    elif flops > 0:
-        pk = fp32_peak if name in fp32_cats else fp64_peak
-        ach = flops / max(launches, 1) / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                "traffic": None, "kernel": name,
-                "peak_source": ("cuBLAS SGEMM" if name in fp32_cats else "cuBLAS DGEMM")
-                               + " 4096^3 measured in this run",
-                "share": ms / tot_ms}
-    else:
-        ach = byts / max(launches, 1) / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
-                "peak_source": f"{peak_kind} hbm_gbs", "share": ms / tot_ms}
-    if roof.get("traffic") is not None:
+    kernels = kernel_table(prof, args.steps)
+    roof = roofline(prof, nrhs, prec == hp.HM_MIXED, peaks, peak_kind, dev)
+    roof["traffic"] = captured_traffic(args.workload, args.precision, nrhs, roof["kernel"])
+    if roof["traffic"] is not None:
         roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this "
-                                  "kernel, one capture of this bench on the same kernel source "
-                                  "(profiles/oz_gather_residual_far_sphere_r2_L5.md)")
+                                  "kernel, one capture of this bench on the same kernel source")
     # ---- end to end through the host-buffer C-ABI call
     Bh = torch.empty((nrhs, sol.N), dtype=torch.complex128, pin_memory=True)
     Bh.copy_(B)
@@ -515,27 +524,31 @@ def run_native(args):
         "clocks": clk.summary(),
         "kernels": kernels,
     }
+    sol64 = None
     if prec == hp.HM_MIXED and not args.no_fp64_compare:
         # the FP64 GPU chain on the same system: the plain two-term series
         # (rate) and the series plus the same FP64 refinement (the like-for-like
         # accuracy comparator of the mixed solve)
         fp64 = {}
-        for refine in (0, 1):
-            sol64 = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max,
-                                    aca_tol=w.aca_tol,
-                                    ordering=hp.HM_ORDER_ND if args.ordering == "nd" else hp.HM_ORDER_DFS,
-                                    precision=hp.HM_FP64, refine_steps=refine)
-            sol64.compute_scaling()
+        for refine in (1, 0):
+            s64 = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max,
+                                  aca_tol=w.aca_tol,
+                                  ordering=hp.HM_ORDER_ND if args.ordering == "nd" else hp.HM_ORDER_DFS,
+                                  precision=hp.HM_FP64, refine_steps=refine)
+            s64.compute_scaling()
             X64 = torch.empty_like(B)
-            sol64.solve(X64, B)
+            s64.solve(X64, B)
             torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(2):
-                sol64.solve(X64, B)
+                s64.solve(X64, B)
             e1.record(stream)
             torch.cuda.synchronize()
             fp64[refine] = (e0.elapsed_time(e1) / 1e3 / 2, X64)
-            del sol64
+            if refine == 0:
+                sol64 = s64          # kept for the single-RHS leg
+            else:
+                del s64
         sol.solve(X, B)
         torch.cuda.synchronize()
         Xr = fp64[1][1]
@@ -548,28 +561,117 @@ def run_native(args):
             "mixed_vs_fp64_refined_rel_err_max": float(d.max().item()),
             "speedup_mixed_over_plain_fp64": value / (nrhs / t64),
             "speedup_mixed_over_fp64_refined": value / (nrhs / fp64[1][0])}
+        del fp64
+    if not args.no_single_rhs:
+        # one RHS (the first of the sweep): the bandwidth-bound form of the
+        # same chain, every block read once per sweep (HBM roofline)
+        single = {}
+        for tag, sh in (("mixed" if prec == hp.HM_MIXED else "fp64", sol), ("fp64", sol64)):
+            if sh is None or tag in single:
+                continue
+            single[tag] = single_rhs_leg(sh, B[:1].contiguous(), max(5, args.steps), peaks,
+                                         peak_kind, stream)
+        line["single_rhs"] = single
     if oracle is not None:
-        proc, conn, procs = oracle
-        res = conn.recv()
-        proc.join()
-        if "error" in res:
-            line["cpu_baseline"] = {"value": None, "unit": "RHS/s", "kind": "oracle",
-                                    "error": res["error"]}
-        else:
-            t = min(res["ts"])
-            line["cpu_baseline"] = {
-                "value": res["n"] / t, "unit": "RHS/s", "cores": res["threads"],
-                "kind": "oracle",
-                "sample": f"{res['n']} of {res['nrhs']} RHS of the same sweep, oracle FP64 "
-                          f"series solve (NumPy), best of 2; oracle set-up "
-                          f"{res['setup_s']:.0f} s untimed ({procs} processes, during the GPU "
-                          "measurement)",
-                "single_thread": one_thread_entry(res)}
+        line["cpu_baseline"] = oracle_result(oracle, "the same sweep")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def kernel_table(prof, steps):
+    tot_ms = sum(p[1] for p in prof.values())
+    kernels = {}
+    for cat, (launches, ms, byts, flops) in prof.items():
+        if not launches:
+            continue
+        kernels[cat] = {"ms_per_step": round(ms / steps, 4), "share": round(ms / tot_ms, 4),
+                        "launches_per_step": int(launches / steps),
+                        "tflops": round(flops / (ms / 1e3) / 1e12, 4),
+                        "gbs": round(byts / (ms / 1e3) / 1e9, 2)}
+    return kernels
+
+
+TENSOR_CATS = ("mixed_sweep", "mixed_far")            # complex64 chain on tcgen05
+OZ_CATS = ("far_stage1", "far_stage2", "near")         # FP64-accurate residual on tcgen05
+FP32_CATS = ("mixed_sweep", "mixed_far")
+
+
+def roofline(prof, nrhs, mixed, peaks, peak_kind, dev):
+    """Roofline of the category with the largest share of the profiled time.
+    With 32 or more RHS the mixed handle's products run on the tensor cores:
+    algorithmic complex-MAC flops (8 per MAC) against the measured bf16 peak
+    (sustained: timed inside a long step).  Below 32 RHS every block is read
+    once per launch for a handful of RHS: algorithmic bytes per launch against
+    the measured HBM copy bandwidth.  FP64 chains with many RHS: FP64 flops
+    against cuBLAS DGEMM measured here."""
+    tot_ms = sum(p[1] for p in prof.values())
+    name, (launches, ms, byts, flops) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / 1e3 / max(1.0, launches)
+    share = ms / tot_ms
+    tc = mixed and nrhs >= 32
+    if flops > 0 and tc and (name in TENSOR_CATS or name in OZ_CATS or name == "dinv"):
+        pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        ach = flops / max(launches, 1) / avg_s / 1e12
+        # executed bf16 flops per algorithmic flop: 6 slice products (three-way
+        # split) or 36 digit products (FP64-accurate slicing)
+        xf = 6.0 if name in TENSOR_CATS else 36.0
+        return {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None, "kernel": name,
+                "peak_source": f"{peak_kind} bf16_tflops_sustained",
+                "note": "achieved counts 8 flops per complex MAC; the kernel executes "
+                        + ("48 bf16 flops per complex MAC (3-way split, 6 slice products, "
+                           "real-expanded complex)" if name in TENSOR_CATS else
+                           "288 bf16 flops per complex MAC (8 digits, 36 slice products)"),
+                "executed_tflops": ach * xf, "executed_frac": ach * xf / pk, "share": share}
+    if nrhs < 32 or flops <= 0:
+        ach = byts / max(launches, 1) / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": name,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "note": "algorithmic bytes per launch (every matrix block once, input and "
+                        "output panels once) over the launch's CUDA-event time",
+                "share": share}
+    import torch
+    fp32 = name in FP32_CATS
+    pk = gemm_peak(dev, torch.float32 if fp32 else torch.float64)
+    ach = flops / max(launches, 1) / avg_s / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": None, "kernel": name,
+            "peak_source": ("cuBLAS SGEMM" if fp32 else "cuBLAS DGEMM")
+                           + " 4096^3 measured in this run", "share": share}
+
+
+def single_rhs_leg(sol, B1, steps, peaks, peak_kind, stream):
+    """Rate of one-RHS solves and the achieved HBM bandwidth of the chain:
+    algorithmic bytes of every launch (the library's per-launch counts) over
+    the device time of the solve, and the roofline of its dominant category."""
+    import torch
+    X1 = torch.empty_like(B1)
+    for _ in range(3):
+        sol.solve(X1, B1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sol.solve(X1, B1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    sol.profile_enable(True)
+    sol.solve(X1, B1)
+    prof = sol.profile()
+    sol.profile_enable(False)
+    byts = sum(p[2] for p in prof.values())
+    launches = int(sum(p[0] for p in prof.values()))
+    roof = roofline(prof, 1, sol.params.precision == 1, peaks, peak_kind, None)
+    return {"value": 1.0 / t, "unit": "RHS/s", "ms_per_solve": 1e3 * t, "steps": steps,
+            "alg_bytes_per_solve": byts, "achieved_gbs": byts / t / 1e9,
+            "hbm_frac": byts / t / 1e9 / peaks["hbm_gbs"], "launches_per_solve": launches,
+            "roofline": roof, "kernels": kernel_table(prof, 1)}
 
 
 # ------------------------------------------------------- grouped scatterer batch
@@ -621,6 +723,7 @@ def run_batch(args):
     for _ in range(max(3, args.warmup)):
         hp.solve_grouped(sols, Xs, Bs)
     torch.cuda.synchronize()
+    oracle_ready(oracle)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(ws)
@@ -730,21 +833,8 @@ def run_batch(args):
         "kernels": kernels,
     }
     if oracle is not None:
-        proc, conn, procs = oracle
-        res = conn.recv()
-        proc.join()
-        if "error" in res:
-            line["cpu_baseline"] = {"value": None, "unit": "RHS/s", "kind": "oracle",
-                                    "error": res["error"]}
-        else:
-            t = min(res["ts"])
-            line["cpu_baseline"] = {
-                "value": res["n"] / t, "unit": "RHS/s", "cores": res["threads"],
-                "kind": "oracle",
-                "sample": f"{res['n']} of {res['nrhs']} RHS of the smallest scatterer "
-                          f"({ws_list[small].name}, N={Ns[small]}), oracle FP64 series "
-                          f"solve (NumPy), best of 2",
-                "single_thread": one_thread_entry(res)}
+        line["cpu_baseline"] = oracle_result(
+            oracle, f"the smallest scatterer ({ws_list[small].name}, N={Ns[small]})")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

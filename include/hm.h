@@ -152,8 +152,9 @@ hm_status hm_plane_wave_rhs(hm_handle h, const double* theta_host, const double*
  * profiling on, and the first failing solve's status otherwise.  A kept graph is
  * rebuilt when a handle's device buffers or schedules have been replaced
  * since it was recorded, and dropped when one of its handles is destroyed.
- * While it runs, a branch uses its handle's work panels: do not run other
- * work on those handles until the stream has reached the graph's end.
+ * The call orders itself after the work already queued on every handle's own
+ * stream, and later work queued on those streams runs after the graph: a
+ * branch uses its handle's work panels.
  * Diagnostics per handle come from hm_get_diagnostics as usual. */
 hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, const int* nrhs,
                            int count);
@@ -204,10 +205,12 @@ hm_status hm_get_profile(hm_handle h, double* out_host, int ncat);
  * far-block ranks) * nrhs complex128 values, lives in a fixed file-scope
  * device array of HM_NOALLOC_SCRATCH_BYTES that every GPU loading the library
  * holds until the process exits.  Returns HM_ERR_INVALID when that scratch
- * would exceed the array (reduce nrhs).  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  Asynchronous on the handle's stream.  All calls
- * share the array: calls whose kernels overlap on the GPU race. */
+ * would exceed the array (reduce nrhs), and also when the current device is
+ * not the handle's.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Asynchronous on the handle's stream.  All calls share the array:
+ * calls whose kernels overlap on the GPU race.  A handle without far blocks
+ * gets Y = 0. */
 #define HM_NOALLOC_SCRATCH_BYTES (32u << 20)
 hm_status hm_apply_far_noalloc(hm_handle h, void* Y, const void* X, int nrhs);
 

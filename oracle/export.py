@@ -18,6 +18,13 @@ float64 pairs; every matrix row-major.
     per rank k: int64 count, int64 j[count]   (the stored row of alpha)
     alpha blocks in that order: complex128 [m_elim[k] * m_elim[j]]
     Dinv per rank: complex128 [m_elim[k] * m_elim[k]]
+  optional sections to the end of the file, each an 8-byte tag and its data:
+    b"LEAFCEN1"  float64 cen[n_leaves * 3]     leaf cell centres (the input of
+                                               the nested-dissection order)
+    b"SUPERND1"  (after scaling only) int64 n_groups, int64 grp[n_groups + 1]
+                 (group g = ranks grp[g] .. grp[g+1]-1), then for every group
+                 with more than one leaf T_G = (I - A_G^T)^-1, complex128
+                 [n_G * n_G] (oracle.scaling.supernode_inverse)
 
 Parity unpinned beyond the round trip: this is a file format, not arithmetic.
 """
@@ -32,7 +39,17 @@ def _c(a):
     return np.ascontiguousarray(a, dtype=np.complex128).tobytes()
 
 
-def write_blocks(path, H, S=None):
+def leaf_centres(H):
+    """Cell centres of the octree leaves, in the unit cube of the root (the
+    coordinates oracle.scaling.nd_order splits on)."""
+    return np.array([[(H.tree.nodes[nid].ijk[a] + 0.5) / (1 << H.tree.nodes[nid].level)
+                      for a in range(3)] for nid in H.tree.leaves], dtype=np.float64)
+
+
+def write_blocks(path, H, S=None, centres=True, groups=None):
+    """``centres``: append the leaf cell centres (when H carries its tree);
+    ``groups``: supernode boundaries in elimination ranks (with S): append
+    the groups and their T_G."""
     m = np.diff(H.leaf_off)
     with open(path, "wb") as f:
         f.write(MAGIC)
@@ -64,6 +81,18 @@ def write_blocks(path, H, S=None):
                     f.write(_c(S.alpha[(k, j)]))
             for k in range(S.n):
                 f.write(_c(S.Dinv[k]))
+        if centres and getattr(H, "tree", None) is not None:
+            f.write(b"LEAFCEN1")
+            f.write(np.ascontiguousarray(leaf_centres(H), dtype="<f8").tobytes())
+        if groups is not None:
+            from .scaling import supernode_inverse
+            assert S is not None and groups[0] == 0 and groups[-1] == S.n
+            f.write(b"SUPERND1")
+            f.write(struct.pack("<q", len(groups) - 1))
+            f.write(np.asarray(groups, dtype="<i8").tobytes())
+            for g in range(len(groups) - 1):
+                if groups[g + 1] - groups[g] > 1:
+                    f.write(_c(supernode_inverse(S, H.leaf_off, groups[g], groups[g + 1])))
 
 
 def read_blocks(path):
@@ -118,5 +147,23 @@ def read_blocks(path):
         dinv = [arr("<c16", me[kk] * me[kk]).reshape(me[kk], me[kk]) for kk in range(nl)]
         assert len(alpha) == na
         out.update(rows=rows, alpha=alpha, Dinv=dinv, elim=elim)
+    while pos < len(buf):
+        tag = buf[pos:pos + 8]
+        pos += 8
+        if tag == b"LEAFCEN1":
+            out["leaf_cen"] = arr("<f8", 3 * nl).reshape(nl, 3)
+        elif tag == b"SUPERND1":
+            assert has_s
+            (ng,) = take("<q")
+            grp = arr("<i8", ng + 1).tolist()
+            me = m[out["elim"]]
+            T = {}
+            for g in range(ng):
+                if grp[g + 1] - grp[g] > 1:
+                    nG = int(np.sum(me[grp[g]:grp[g + 1]]))
+                    T[g] = arr("<c16", nG * nG).reshape(nG, nG)
+            out.update(groups=grp, T=T)
+        else:
+            raise ValueError(f"unknown section {tag!r}")
     assert pos == len(buf)
     return out

@@ -90,11 +90,16 @@ def symbolic_fill_naive(n, near_pairs):
     return [sorted(r) for r in rows]
 
 
-def nd_order(tree, near_pairs, min_size=4):
+def nd_order(tree, near_pairs, min_size=4, with_groups=False):
     """Geometric nested dissection of the leaf graph (near pairs = edges):
     split the leaves at the median (ties by leaf number) of the widest axis of
     their cell centres; the separator is the part of the first half adjacent
-    to the second; order = ND(first - separator), ND(second), separator."""
+    to the second; order = ND(first - separator), ND(second), separator.
+
+    ``with_groups``: also return the supernode boundaries in ranks, a list
+    g_0 = 0 < g_1 < ... = n where every group [g_i, g_i+1) is one bottom set
+    of at most ``min_size`` leaves or one separator (ranks of a group are
+    consecutive)."""
     n = tree.n_leaves
     adj = [set() for _ in range(n)]
     for (i, j) in near_pairs:
@@ -106,10 +111,12 @@ def nd_order(tree, near_pairs, min_size=4):
         nd = tree.nodes[nid]
         cen.append([(nd.ijk[a] + 0.5) / (1 << nd.level) for a in range(3)])
     cen = np.array(cen)
-    order = []
+    order, groups = [], []
 
     def rec(ids):
         if len(ids) <= min_size:
+            if ids:
+                groups.append(len(order))
             order.extend(sorted(ids))
             return
         ext = [cen[ids, a].max() - cen[ids, a].min() for a in range(3)]
@@ -122,9 +129,13 @@ def nd_order(tree, near_pairs, min_size=4):
         sset = set(sep)
         rec(sorted(i for i in first if i not in sset))
         rec(sorted(second))
+        if sep:
+            groups.append(len(order))
         order.extend(sep)
 
     rec(list(range(n)))
+    if with_groups:
+        return order, groups + [n]
     return order
 
 
@@ -188,6 +199,27 @@ def compute_scaling(H, reading="A", order=None):
             del Zt[(k, j)]
     return Scaling(n=n, rows=rows, alpha=alpha, D=D, Dinv=Dinv, reading=reading,
                    order=order)
+
+
+def supernode_inverse(S, leaf_off, g0, g1):
+    """T_G = (I - A_G^T)^{-1} of the consecutive ranks G = g0 .. g1-1, where
+    A_G holds the blocks alpha_kj (k < j, both in G).  Restricted to the rows
+    of G, the forward substitution of Eq. 25 reads b~_G = b_G + A_G^T b~_G +
+    (terms from ranks before g0), so T_G maps the right-hand side of G, with
+    its outside contributions added, to b~_G.  Row-major n_G x n_G, rows and
+    columns in rank order (block of rank k at the sum of the sizes of ranks
+    g0 .. k-1).  Dense inverse (numpy.linalg.inv); tests and the block file
+    only."""
+    m = np.diff(leaf_off)[S.order]
+    off = np.concatenate([[0], np.cumsum(m[g0:g1])])
+    nG = int(off[-1])
+    A = np.zeros((nG, nG), np.complex128)
+    for k in range(g0, g1):
+        for j in S.rows[k]:
+            if j < g1:
+                a, b = k - g0, j - g0
+                A[off[a]:off[a + 1], off[b]:off[b + 1]] = S.alpha[(k, j)]
+    return np.linalg.inv(np.eye(nG) - A.T)
 
 
 # ------------------------------------------------------------ applications

@@ -1008,8 +1008,55 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
       h->has_scaling = true;
       h->p.fill = (reading == 1) ? HM_FILL_NEAR : HM_FILL_FULL;
     }
-    char extra;
-    if (!r.ok || fread(&extra, 1, 1, f) != 0) throw std::runtime_error("size");
+    if (!r.ok) throw std::runtime_error("size");
+    // optional trailing sections, each introduced by an 8-byte tag
+    for (;;) {
+      char tag[8];
+      const size_t got = fread(tag, 1, 8, f);
+      if (got == 0 && feof(f)) break;
+      if (got != 8) throw std::runtime_error("tag");
+      if (memcmp(tag, "LEAFCEN1", 8) == 0) {
+        // leaf cell centres (input of the nested-dissection order)
+        h->leaf_cen.resize(3 * (size_t)nl);
+        r.get(h->leaf_cen.data(), h->leaf_cen.size());
+        if (!r.ok) throw std::runtime_error("centres");
+        for (double c : h->leaf_cen)
+          if (!std::isfinite(c)) throw std::runtime_error("centres");
+      } else if (memcmp(tag, "SUPERND1", 8) == 0) {
+        // supernode groups of consecutive ranks and T_G = (I - A_G^T)^-1 of
+        // every group with more than one leaf (row-major n_G x n_G)
+        if (!h->has_scaling) throw std::runtime_error("groups without scaling");
+        const long long ng = r.q();
+        if (!r.ok || ng < 1 || ng > nl) throw std::runtime_error("groups");
+        std::vector<long long> g(ng + 1);
+        r.get(g.data(), g.size());
+        if (!r.ok || g[0] != 0 || g[ng] != nl) throw std::runtime_error("groups");
+        for (long long q = 0; q < ng; ++q)
+          if (g[q + 1] <= g[q]) throw std::runtime_error("groups");
+        h->grp.assign(g.begin(), g.end());
+        h->tg_off.assign(ng, 0);
+        h->tg_n.assign(ng, 0);
+        h->rloc.assign(nl, 0);
+        long long nt_all = 0;
+        for (long long q = 0; q < ng; ++q) {
+          int nG = 0;
+          for (long long k = g[q]; k < g[q + 1]; ++k) {
+            h->rloc[k] = nG;
+            nG += h->m[h->elim[k]];
+          }
+          h->tg_off[q] = nt_all;
+          if (g[q + 1] - g[q] > 1) {
+            h->tg_n[q] = nG;
+            nt_all += (long long)nG * nG;
+          }
+        }
+        h->h_tinv.resize(nt_all);
+        r.get(h->h_tinv.data(), h->h_tinv.size());
+        if (!r.ok) throw std::runtime_error("supernodes");
+      } else {
+        throw std::runtime_error("section");
+      }
+    }
     fclose(f);
     f = nullptr;
     s = upload_values(h);
@@ -1083,6 +1130,21 @@ hm_status hm_save(hm_handle h, const char* path) {
     for (int k = 0; k < h->nl; ++k)
       ok = ok && put(h->h_dinv.data() + h->dinv_off[k],
                      (size_t)h->m[h->elim[k]] * h->m[h->elim[k]] * sizeof(cplx));
+  }
+  if ((long long)h->leaf_cen.size() == 3LL * h->nl) {
+    ok = ok && put("LEAFCEN1", 8) && put(h->leaf_cen.data(), h->leaf_cen.size() * sizeof(double));
+  }
+  if (h->has_scaling && has_groups(h)) {
+    const long long ng = (long long)h->grp.size() - 1;
+    ok = ok && put("SUPERND1", 8) && put(&ng, 8);
+    for (int g : h->grp) {
+      long long gg = g;
+      ok = ok && put(&gg, 8);
+    }
+    for (long long g = 0; g < ng; ++g)
+      if (h->tg_n[g])
+        ok = ok && put(h->h_tinv.data() + h->tg_off[g],
+                       (size_t)h->tg_n[g] * h->tg_n[g] * sizeof(cplx));
   }
   ok = (fclose(f) == 0) && ok;
   return ok ? HM_OK : HM_ERR_IO;

@@ -7,6 +7,7 @@
 // per problem; every call launches the instantiated graph on the caller's
 // stream (one launch for the whole batch; the GPU overlaps the branches'
 // kernels).
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -83,6 +84,41 @@ hm_status capture(hm_handle* hs, void** X, const void** B, const int* nrhs, int 
   return HM_OK;
 }
 
+// Cross-stream ordering of a grouped call that runs on `main`: with
+// before = true, main waits for the work already queued on every other handle
+// stream (a branch reuses its handle's work panels); with before = false,
+// every other handle stream waits for what main has queued so far (later work
+// on a handle starts after the graph).  One event per crossing, destroyed
+// right away (the runtime keeps it until the wait is satisfied).
+hm_status order_streams(hm_handle* hs, int count, cudaStream_t main, bool before) {
+  std::vector<cudaStream_t> seen;
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t si = hs[i]->stream;
+    if (si == main || std::find(seen.begin(), seen.end(), si) != seen.end()) continue;
+    seen.push_back(si);
+  }
+  if (seen.empty()) return HM_OK;
+  if (before) {
+    for (cudaStream_t si : seen) {
+      cudaEvent_t e;
+      HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      cudaError_t r = cudaEventRecord(e, si);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(main, e, 0);
+      cudaEventDestroy(e);
+      HM_CUDA(r);
+    }
+  } else {
+    cudaEvent_t e;
+    HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, main);
+    for (cudaStream_t si : seen)
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(si, e, 0);
+    cudaEventDestroy(e);
+    HM_CUDA(r);
+  }
+  return HM_OK;
+}
+
 }  // namespace
 
 extern "C" hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, const int* nrhs,
@@ -104,6 +140,8 @@ extern "C" hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, c
     key.push_back((const void*)(long long)nrhs[i]);
   }
   std::lock_guard<std::mutex> lk(g_mu);
+  hm_status so = order_streams(hs, count, main, true);
+  if (so != HM_OK) return so;
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
     bool stale = false;
@@ -134,7 +172,7 @@ extern "C" hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, c
     it = g_cache.emplace(key, gg).first;
   }
   HM_CUDA(cudaGraphLaunch(it->second.exec, main));
-  return HM_OK;
+  return order_streams(hs, count, main, false);
 }
 
 namespace hm {

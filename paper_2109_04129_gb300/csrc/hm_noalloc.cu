@@ -29,12 +29,12 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_scr[MAX_DEVICES] = {nullptr};
 
-// Device address of the scratch array on the current device: looked up with
-// cudaGetSymbolAddress once per device (the name is only a host-side
-// stand-in for the symbol and cannot be passed to a kernel).
-hm_status scratch_ptr(double2** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return HM_ERR_CUDA;
+// Device address of the scratch array on device dev, which must be the
+// current device: looked up with cudaGetSymbolAddress once per device (the
+// name is only a host-side stand-in for the symbol and cannot be passed to a
+// kernel).
+hm_status scratch_ptr(int dev, double2** out) {
+  if (dev < 0 || dev >= MAX_DEVICES) return HM_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scr[dev]) {
     void* p = nullptr;
@@ -102,11 +102,18 @@ __global__ void k_na_far2(const GTask* __restrict__ tasks, const GItem* __restri
 
 extern "C" hm_status hm_apply_far_noalloc(hm_handle h, void* Y, const void* X, int nrhs) {
   if (!h || !Y || !X || nrhs <= 0) return HM_ERR_INVALID;
-  if (!h->sched_ready || !h->d_far) return HM_ERR_STATE;
+  if (!h->sched_ready) return HM_ERR_STATE;
   if ((size_t)h->far_t_rows * (size_t)nrhs > NA_ELEMS) return HM_ERR_INVALID;
+  // the kernels run on the handle's stream, which belongs to the handle's
+  // device: that device must be current
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return HM_ERR_CUDA;
+  if (cur != h->dev) return HM_ERR_INVALID;
   double2* T = nullptr;
-  hm_status s = scratch_ptr(&T);
+  hm_status s = scratch_ptr(h->dev, &T);
   if (s) return s;
+  // a handle without far blocks (one leaf, or every pair near) has no stage-1
+  // tasks; stage 2 still runs one task per leaf and writes Y = 0
   if (!h->far1_tl.tasks.empty())
     k_na_far1<<<(unsigned)h->far1_tl.tasks.size(), 256, 0, h->stream>>>(
         h->far1_tl.d_tasks, h->far1_tl.d_items, h->d_far, (const double2*)X, h->d_perm, h->N,

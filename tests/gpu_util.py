@@ -8,12 +8,14 @@ import numpy as np
 from oracle.export import write_blocks
 
 
-def load_case(H, S, **kw):
+def load_case(H, S, groups=None, **kw):
+    """Export the oracle's H (and scaling S, and supernode groups with their
+    T_G) and load it in the library with solve options kw."""
     import paper_2109_04129_gb300 as hp
     fd, path = tempfile.mkstemp(suffix=".hmps")
     os.close(fd)
     try:
-        write_blocks(path, H, S)
+        write_blocks(path, H, S, groups=groups)
         return hp.Solver.load(path, **kw)
     finally:
         os.unlink(path)

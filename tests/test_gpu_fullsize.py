@@ -3,7 +3,10 @@ N = 30720, leaves <= 128, ACA 1e-4, nested-dissection elimination order),
 all 362 monostatic right-hand sides in one call (the launch configuration
 bench.py times: tensor-core mixed chain and FP64-accurate tensor residual for
 nrhs >= 32).  The oracle builds its own H-matrix and scaling (plain C entries,
-spawn pool), the GPU imports them; the oracle solves a sample of 6 columns.
+spawn pool).  The GPU imports the H-matrix and either the oracle's scaling
+(leaf-level sweeps; the oracle solves a sample of 6 columns) or none, when it
+runs its own nested-dissection scaling with supernode sweeps, the schedule
+bench.py times (every column compared).
 
 Bars: FP64 chain <= 1e-6, mixed chain + refinement <= 1e-4 (against the
 oracle's FP64 series + refinement), per sampled RHS."""
@@ -40,7 +43,7 @@ def _load(H, S, **kw):
     fd, path = tempfile.mkstemp(suffix=".hmps")
     os.close(fd)
     try:
-        write_blocks(path, H, S)
+        write_blocks(path, H, S)     # with the leaf centres (nested dissection)
         return hp.Solver.load(path, **kw)
     finally:
         os.unlink(path)
@@ -70,6 +73,58 @@ def test_full_size_fp64_and_mixed(full_case):
     errm = rel(from_dev(Xm)[:, cols], xr)
     assert errm.max() <= 1e-4, errm
     print(f"full size: FP64 max rel err {err64.max():.2e}, mixed {errm.max():.2e}")
+
+
+def test_full_size_benchmarked_schedule(full_case):
+    """The schedule bench.py times, on all 362 RHS: the library orders the
+    leaves by nested dissection, groups the ranks into supernodes and builds
+    alpha, D^-1 and T_G itself (hm_compute_scaling on the GPU, from the
+    oracle's H-matrix and leaf centres); then the FP64 chain and the mixed
+    chain (tcgen05 sweeps over the supernodes, tcgen05 far field, FP64-accurate
+    residual, split-K up to 4096 rows) solve every RHS, compared with the
+    oracle's series and series + refinement on the same H in the same order."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from oracle.export import read_blocks
+    from oracle.scaling import nd_order, supernode_inverse
+    from oracle.series import series_solve, refine_once
+    w, H, S, B = full_case
+    order, groups = nd_order(H.tree, list(H.near.keys()), with_groups=True)
+    assert list(S.order) == order
+    sol = _load(H, None, ordering=hp.HM_ORDER_ND)
+    sol.compute_scaling()
+    fd, path = tempfile.mkstemp(suffix=".hmps")
+    os.close(fd)
+    try:
+        sol.save(path)
+        d = read_blocks(path)
+    finally:
+        os.unlink(path)
+    assert d["elim"] == order and d["rows"] == S.rows and d["groups"] == groups
+    sa = max(np.abs(a).max() for a in S.alpha.values())
+    ea = max(np.abs(d["alpha"][k] - S.alpha[k]).max() for k in S.alpha) / sa
+    assert ea < 1e-9, ea
+    big = sorted(d["T"], key=lambda g: -d["T"][g].shape[0])[:3]
+    for g in big:
+        want = supernode_inverse(S, H.leaf_off, groups[g], groups[g + 1])
+        assert np.abs(d["T"][g] - want).max() <= 1e-9 * np.abs(want).max(), g
+    del d
+    x2, _ = series_solve(H, S, B, 2)
+    Bd = to_dev(B)
+    X = torch.empty_like(Bd)
+    sol.solve(X, Bd)
+    err64 = rel(from_dev(X), x2)
+    assert err64.max() <= 1e-6, err64.max()
+    del sol
+    xr = refine_once(H, S, B, x2)
+    solm = _load(H, None, ordering=hp.HM_ORDER_ND, precision=hp.HM_MIXED, refine_steps=1)
+    solm.compute_scaling()
+    Xm = torch.empty_like(Bd)
+    solm.solve(Xm, Bd)
+    errm = rel(from_dev(Xm), xr)
+    assert errm.max() <= 1e-4, errm.max()
+    print(f"benchmarked schedule, 362 RHS: FP64 max rel err {err64.max():.2e}, "
+          f"mixed {errm.max():.2e}")
 
 
 def test_full_size_native_build_properties(full_case):

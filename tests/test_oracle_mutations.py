@@ -203,6 +203,21 @@ def pin_sweeps(sc):
                 np.allclose(sc.apply_Rt(S, H.leaf_off, x), R.T @ x, atol=1e-12))
 
 
+def pin_supernodes(sc):
+    """T_G b_G equals the forward substitution (Eq. 25) of b supported on the
+    consecutive ranks G, restricted to G."""
+    pat = [(i, i) for i in range(6)] + [(0, 2), (0, 4), (1, 3), (2, 5), (3, 4), (1, 5)]
+    rng, H, _ = _sym_case(7, [2, 3, 1, 4, 2, 3], pat)
+    S = sc.compute_scaling(H, "A")
+    g0, g1 = 1, 5
+    T = sc.supernode_inverse(S, H.leaf_off, g0, g1)
+    s0, s1 = int(H.leaf_off[g0]), int(H.leaf_off[g1])
+    b = np.zeros((H.N, 2), np.complex128)
+    b[s0:s1] = rng.standard_normal((s1 - s0, 2)) + 1j * rng.standard_normal((s1 - s0, 2))
+    y = sc.apply_Rt(S, H.leaf_off, b)
+    return bool(np.allclose(T @ b[s0:s1], y[s0:s1], atol=1e-12))
+
+
 _LU = {}
 
 
@@ -335,6 +350,10 @@ MUTANTS = [
     ("back_sweep_sign", "scaling", pin_sweeps,
      "out[sl[k]] += S.alpha[(k, j)] @ out[sl[j]]",
      "out[sl[k]] -= S.alpha[(k, j)] @ out[sl[j]]"),
+    ("supernode_not_transposed", "scaling", pin_supernodes,
+     "return np.linalg.inv(np.eye(nG) - A.T)", "return np.linalg.inv(np.eye(nG) - A)"),
+    ("supernode_sign", "scaling", pin_supernodes,
+     "return np.linalg.inv(np.eye(nG) - A.T)", "return np.linalg.inv(np.eye(nG) + A.T)"),
     ("series_alternating_sign", "series", pin_series,
      "xt = xt + ((-1) ** n) * nxt", "xt = xt + nxt"),
     ("series_dropped_dinv", "series", pin_series,
