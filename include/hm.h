@@ -70,12 +70,20 @@ typedef struct {
   int fp64_emulation;    /* HM_MIXED refinement residual (FP64-accurate products)
                             on tensor cores by exact 7-bit integer slicing of the
                             FP64 operands: 1 (default), or 0 for the FP64 units  */
-  int reserved[6];
+  double term_tol;       /* 0 (default): exactly n_terms terms of Eq. 36.  > 0:
+                            adaptive term count (Sec. III-C, Eq. 44-45): after
+                            each term it_t, t >= 1, the series stops when every
+                            RHS has ||it_t|| <= term_tol ||it_0|| (converged),
+                            or when some RHS has ||it_t|| >= ||it_(t-1)|| (its
+                            terms no longer shrink: the ratio of Eq. 45 is at
+                            least one), and at n_terms terms in any case.  The
+                            solve then synchronises its stream once per term.  */
+  int reserved[4];
 } hm_params;
 
 /* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,
  * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26, tensor_cores 1,
- * fp64_emulation 1. */
+ * fp64_emulation 1, term_tol 0 (fixed term count). */
 void hm_default_params(hm_params* p);
 
 /* Build the H-matrix of a closed or open triangulated PEC surface (Sec. II:
@@ -148,8 +156,10 @@ hm_status hm_plane_wave_rhs(hm_handle h, const double* theta_host, const double*
  * graph with one branch per problem and keeps the instantiated graph; every
  * call, the first included, then launches that graph on the first handle's
  * stream (asynchronous).  Returns HM_ERR_INVALID for null or repeated handles
- * or non-positive counts, HM_ERR_STATE for a handle without scaling or with
- * profiling on, and the first failing solve's status otherwise.  A kept graph is
+ * or non-positive counts, HM_ERR_STATE for a handle without scaling, with
+ * profiling on or with an adaptive term count (term_tol > 0: its host-side
+ * decisions cannot be recorded), and the first failing solve's status
+ * otherwise.  A kept graph is
  * rebuilt when a handle's device buffers or schedules have been replaced
  * since it was recorded, and dropped when one of its handles is destroyed.
  * The call orders itself after the work already queued on every handle's own
@@ -172,9 +182,10 @@ hm_status hm_get_diagnostics(hm_handle h, double* ratio_host, double* resid_host
 /* Counts, as long long, in this order (up to n of them): N, leaves, near
  * blocks (upper), far blocks (upper), alpha entries, D entries, near entries
  * (upper), far factor entries, max rank, forward levels, backward levels,
- * device bytes held, and the number of kernels the library has launched in
+ * device bytes held, the number of kernels the library has launched in
  * this process so far (all handles; read it before and after a region to
- * count that region's launches). */
+ * count that region's launches), and the number of series terms of the last
+ * solve (the largest over its series when refinement steps ran). */
 hm_status hm_get_stats(hm_handle h, long long* out_host, int n);
 
 /* Copy the leaf-order permutation (N int64, leaf position -> original index)

@@ -30,6 +30,31 @@ hm_status cuda_status(cudaError_t e) {
   return HM_ERR_CUDA;
 }
 
+hm_status term_norms(hm_ctx* h, const void* v, bool f32, int nrhs, std::vector<double>& out) {
+  double* d = h->d_norms + 4 * (size_t)nrhs;          // the fifth slot of the norm buffer
+  hm_status s = f32 ? launch_col_norms2_32((const float2*)v, h->N, nrhs, d, h->stream)
+                    : launch_col_norms2((const cplx*)v, h->N, nrhs, d, h->stream);
+  if (s) return s;
+  out.assign(nrhs, 0.0);
+  HM_CUDA(cudaMemcpyAsync(out.data(), d, nrhs * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+  HM_CUDA(cudaStreamSynchronize(h->stream));
+  return HM_OK;
+}
+
+// Adaptive term count (Sec. III-C, Eq. 44-45), on squared norms: stop after
+// the latest term it_t when every RHS has ||it_t|| <= tol ||it_0||, or when
+// some RHS has ||it_t|| >= ||it_(t-1)|| > 0 (no longer shrinking).
+bool terms_stop(const std::vector<double>& n0, const std::vector<double>& nprev,
+                const std::vector<double>& nt, double tol) {
+  bool conv = true, grow = false;
+  for (size_t r = 0; r < nt.size(); ++r) {
+    if (nt[r] > tol * tol * n0[r]) conv = false;
+    if (nt[r] > 0.0 && nt[r] >= nprev[r]) grow = true;
+  }
+  return conv || grow;
+}
+
 int prof_begin(hm_ctx* h) {
   if (!h->prof) return -1;
   while (h->evpool.size() < h->evused + 2) {
@@ -556,7 +581,7 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
     HM_CUDA(cudaMalloc((void**)&h->d_vec[i], rows[i] * nrhs * sizeof(cplx)));
     h->vec_rows[i] = rows[i];
   }
-  HM_CUDA(cudaMalloc((void**)&h->d_norms, 4 * sizeof(double) * nrhs));
+  HM_CUDA(cudaMalloc((void**)&h->d_norms, 5 * sizeof(double) * nrhs));
   cudaFree(h->d_fexp);
   HM_CUDA(cudaMalloc((void**)&h->d_fexp, 2 * sizeof(int) * nrhs));
   for (int i = 0; i < 2; ++i) {
@@ -798,6 +823,11 @@ hm_status series_fp64(hm_ctx* h, int nrhs, bool diag) {
   if ((s = run_list(h, h->dinv_tl, V[P_Y], V[P_BO], nrhs, PC_DINV))) return s;
   if ((s = copy_panel(h, V[P_XT], V[P_BO], nrhs))) return s;
   cplx* it = V[P_BO];
+  const bool adapt = h->p.term_tol > 0.0;
+  std::vector<double> n0, nprev, nt;
+  if (adapt && h->p.n_terms > 1 && (s = term_norms(h, it, false, nrhs, n0))) return s;
+  nprev = n0;
+  int used = 1;
   for (int t = 1; t < h->p.n_terms; ++t) {
     // it_t = D^-1 R^T Z_F R it_{t-1}
     if ((s = copy_panel(h, V[P_Y], it, nrhs))) return s;
@@ -814,7 +844,14 @@ hm_status series_fp64(hm_ctx* h, int nrhs, bool diag) {
     if ((s = launch_axpby(V[P_XT], V[P_XT], 1.0, nxt, sg, (size_t)h->N * nrhs, h->stream)))
       return s;
     it = nxt;
+    used = t + 1;
+    if (adapt) {
+      if ((s = term_norms(h, nxt, false, nrhs, nt))) return s;
+      if (terms_stop(n0, nprev, nt, h->p.term_tol)) break;
+      nprev.swap(nt);
+    }
   }
+  h->last_terms = std::max(h->last_terms, used);
   // x = R x~
   return run_sweep(h, h->bwd, V[P_XT], nrhs, PC_BWD);
 }
@@ -1218,8 +1255,10 @@ hm_status hm_power_series_solve(hm_handle h, void* X, const void* B, int nrhs) {
   if (s) return s;
   if (!X || !B || nrhs <= 0) return HM_ERR_INVALID;
   if (h->p.n_terms < 1) return HM_ERR_INVALID;
+  if (h->p.term_tol < 0.0) return HM_ERR_INVALID;
   try {
     if ((s = ensure_buffers(h, nrhs))) return s;
+    h->last_terms = 0;
     if (h->p.precision == HM_MIXED) {
       s = hm_mixed_solve(h, (cplx*)X, (const cplx*)B, nrhs);
     } else {
@@ -1321,10 +1360,11 @@ hm_status hm_get_stats(hm_handle h, long long* out, int n) {
   for (int k = 0; k < (int)h->rows.size(); ++k)
     for (int j : h->rows[k]) a_e += (long long)h->m[h->elim[k]] * h->m[h->elim[j]];
   for (int k = 0; k < h->nl; ++k) d_e += (long long)h->m[k] * h->m[k];
-  long long v[13] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
+  long long v[14] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
                      near_e, far_e, maxr, (long long)h->fwd.part.size(),
-                     (long long)h->bwd.part.size(), (long long)h->dev_bytes, hm::launch_count()};
-  for (int i = 0; i < n && i < 13; ++i) out[i] = v[i];
+                     (long long)h->bwd.part.size(), (long long)h->dev_bytes, hm::launch_count(),
+                     h->last_terms};
+  for (int i = 0; i < n && i < 14; ++i) out[i] = v[i];
   return HM_OK;
 }
 

@@ -128,6 +128,7 @@ extern "C" hm_status hm_solve_grouped(hm_handle* hs, void** X, const void** B, c
     if (!hs[i] || !X[i] || !B[i] || nrhs[i] <= 0) return HM_ERR_INVALID;
     if (!hs[i]->has_scaling || !hs[i]->sched_ready) return HM_ERR_STATE;
     if (hs[i]->prof) return HM_ERR_STATE;        // per-launch timing events cannot be captured
+    if (hs[i]->p.term_tol > 0.0) return HM_ERR_STATE;   // host decisions per term
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return HM_ERR_INVALID;  // a handle's work panels serve one solve
   }

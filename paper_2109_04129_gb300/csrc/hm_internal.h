@@ -179,6 +179,7 @@ struct hm_ctx {
   std::vector<hm::ProfRec> recs;
   size_t evused = 0;
   std::vector<double> ratio, resid;
+  int last_terms = 0;           // series terms of the last solve (largest over its series)
   size_t dev_bytes = 0;
   // bumped whenever device buffers or task lists are replaced; a grouped-solve
   // graph captured under another value refers to freed memory and is rebuilt
@@ -257,6 +258,13 @@ hm_status launch_plane_wave(const double* d_verts, const int* d_tris, const int*
                             cudaStream_t s);
 // api.cu helpers
 hm_status cuda_status(cudaError_t e);
+// adaptive term count: squared column norms of a leaf-order panel (complex128,
+// or complex64 when f32) copied to the host (synchronises the stream), and the
+// stopping rule of hm_params.term_tol on the squared norms of the first, the
+// previous and the latest term
+hm_status term_norms(hm_ctx* h, const void* v, bool f32, int nrhs, std::vector<double>& out);
+bool terms_stop(const std::vector<double>& n0, const std::vector<double>& nprev,
+                const std::vector<double>& nt, double tol);
 int prof_begin(hm_ctx* h);                                   // -1 when disabled
 void prof_end(hm_ctx* h, int ev, int cat, double bytes, double flops);
 // kernels launched by the library in this process (hm_get_stats)

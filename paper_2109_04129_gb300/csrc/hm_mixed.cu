@@ -95,6 +95,13 @@ hm_status series32(hm_ctx* h, Mixed* M, int nrhs, bool diag) {
   if ((s = dinv32(h, V[Q_Y], V[Q_BO], nrhs))) return s;
   if ((s = copy32(h, V[Q_XT], V[Q_BO], nrhs))) return s;
   float2* it = V[Q_BO];
+  // adaptive term count (hm_params.term_tol): the rule of the FP64 chain on
+  // the complex64 terms
+  const bool adapt = h->p.term_tol > 0.0;
+  std::vector<double> n0, nprev, nt;
+  if (adapt && h->p.n_terms > 1 && (s = term_norms(h, it, true, nrhs, n0))) return s;
+  nprev = n0;
+  int used = 1;
   for (int t = 1; t < h->p.n_terms; ++t) {
     if ((s = copy32(h, V[Q_Y], it, nrhs))) return s;
     if ((s = run_chain_sweep(h, h->bwd, V[Q_Y], nrhs, PC_MX_SWEEP, PREC_32, true))) return s;
@@ -110,7 +117,14 @@ hm_status series32(hm_ctx* h, Mixed* M, int nrhs, bool diag) {
     if ((s = launch_axpby32(V[Q_XT], V[Q_XT], 1.0f, nxt, sg, (size_t)h->N * nrhs, h->stream)))
       return s;
     it = nxt;
+    used = t + 1;
+    if (adapt) {
+      if ((s = term_norms(h, nxt, true, nrhs, nt))) return s;
+      if (terms_stop(n0, nprev, nt, h->p.term_tol)) break;
+      nprev.swap(nt);
+    }
   }
+  h->last_terms = std::max(h->last_terms, used);
   return run_chain_sweep(h, h->bwd, V[Q_XT], nrhs, PC_MX_SWEEP, PREC_32, true);
 }
 
@@ -220,7 +234,8 @@ static hm_status residual_products(hm_ctx* h, int nrhs, bool with_far) {
 
 hm_status hm_mixed_solve(hm_ctx* h, cplx* X, const cplx* B, int nrhs) {
   Mixed* M = (Mixed*)h->mixed;
-  if (!M || !M->alpha) return HM_ERR_STATE;
+  // (a handle with one leaf has scaling but no alpha blocks: M->alpha is null)
+  if (!M || !h->has_scaling) return HM_ERR_STATE;
   hm_status s = ensure32(h, M, nrhs);
   if (s) return s;
   cplx** V = h->d_vec;
@@ -253,7 +268,7 @@ hm_status hm_mixed_solve(hm_ctx* h, cplx* X, const cplx* B, int nrhs) {
 hm_status hm_mixed_apply(hm_ctx* h, int op, cplx* Y, const cplx* X, int nrhs) {
   Mixed* M = (Mixed*)h->mixed;
   if (!M) return HM_ERR_STATE;
-  if ((op == HM_OP_RT || op == HM_OP_R) && !M->alpha) return HM_ERR_STATE;
+  if ((op == HM_OP_RT || op == HM_OP_R) && !h->has_scaling) return HM_ERR_STATE;
   hm_status s = ensure32(h, M, nrhs);
   if (s) return s;
   cplx** V = h->d_vec;

@@ -231,3 +231,27 @@ def test_phi_polarised_wave_matches_mie_h_plane():
     m = mie_bistatic(0.5, E.k, np.pi - th, "H")
     db = 10 * np.log10(s / m)
     assert np.abs(db).max() < 0.5, db
+
+
+def test_adaptive_term_count_follows_tolerance():
+    """Adaptive term count (Sec. III-C, Eq. 44-45) on the converging plate
+    (ratio about 0.4): the error against the LU solution of the assembled
+    H-matrix follows the tolerance, with more terms for a tighter one; on
+    the 0.5 lambda sphere, where the terms eventually grow (spectral radius
+    above one), the series stops at the first growing term, long before the cap."""
+    H, S, B = plate_converging()
+    x_lu = np.linalg.solve(H.to_dense(), B[H.perm])
+    X = np.empty_like(x_lu)
+    X[H.perm] = x_lu
+    terms = []
+    for tol in (1e-3, 1e-6, 1e-10):
+        x, ratios = series_solve(H, S, B, 60, term_tol=tol)
+        terms.append(len(ratios) + 1)
+        assert np.all(rel_err(x, X) < 10 * tol), (tol, rel_err(x, X))
+        assert np.all(ratios < 1.0)
+    assert terms[0] < terms[1] < terms[2] < 60
+    w, Hs, Ss, Bs = case("sphere_r0.5_L3")
+    with np.errstate(all="ignore"):
+        x, ratios = series_solve(Hs, Ss, Bs, 60, term_tol=1e-8)
+    assert len(ratios) + 1 < 60
+    assert np.any(ratios[-1] >= 1.0) and np.all(ratios[:-1] < 1.0)
