@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-single-rhs", action="store_true",
                     help="skip the one-RHS (bandwidth-bound) leg")
     ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
+    ap.add_argument("--levels", type=int, nargs="+", default=[3, 4, 5, 6],
+                    help="icosphere levels of --workload sphere_scaling")
     ap.add_argument("--batch-count", type=int, default=64,
                     help="scatterers in --workload scatterer_batch")
     return ap.parse_args()
@@ -661,6 +663,20 @@ def single_rhs_leg(sol, B1, steps, peaks, peak_kind, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / steps
+    # the same solve replayed from a CUDA graph (the grouped entry point with
+    # one problem): no host launch overhead between the chain's ~140-280 launches
+    import paper_2109_04129_gb300 as hp
+    Xg = torch.empty_like(B1)
+    for _ in range(3):
+        hp.solve_grouped([sol], [Xg], [B1])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        hp.solve_grouped([sol], [Xg], [B1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tg = e0.elapsed_time(e1) / 1e3 / steps
+    same = bool(torch.equal(Xg, X1))
     sol.profile_enable(True)
     sol.solve(X1, B1)
     prof = sol.profile()
@@ -671,6 +687,10 @@ def single_rhs_leg(sol, B1, steps, peaks, peak_kind, stream):
     return {"value": 1.0 / t, "unit": "RHS/s", "ms_per_solve": 1e3 * t, "steps": steps,
             "alg_bytes_per_solve": byts, "achieved_gbs": byts / t / 1e9,
             "hbm_frac": byts / t / 1e9 / peaks["hbm_gbs"], "launches_per_solve": launches,
+            "graph": {"value": 1.0 / tg, "ms_per_solve": 1e3 * tg,
+                      "achieved_gbs": byts / tg / 1e9,
+                      "hbm_frac": byts / tg / 1e9 / peaks["hbm_gbs"],
+                      "equals_stream_solve": same},
             "roofline": roof, "kernels": kernel_table(prof, 1)}
 
 
@@ -752,6 +772,7 @@ def run_batch(args):
     t_seq, v_seq = job_rate(ws, nrhs_tot, e0.elapsed_time(e1) / 1e3 / args.steps, dev)
     same = all(torch.equal(X, Y) for X, Y in zip(Xs, Ys))
     ratio_max = max(float(np.max(s.diagnostics(B.shape[0])[0])) for s, B in zip(sols, Bs))
+    accuracy = batch_accuracy(sols, Xs, Bs, ws_list) if prec == hp.HM_MIXED else None
     # per-kernel timing: one profiled pass of the single solves (events around
     # every launch cannot be recorded in the graph)
     tot = {}
@@ -826,6 +847,7 @@ def run_batch(args):
         "gpu_launches": launches_per_step * args.steps,
         "graph_launches": args.steps,
         "clocks": clk.summary(),
+        "accuracy": accuracy,
         "sequential": {"value": v_seq, "unit": "RHS/s",
                        "ms_per_step": 1e3 * t_seq,
                        "what": "the same solves issued one after another, no graph",
@@ -842,10 +864,123 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- scaling study (set-up / solve vs N)
+SCALING_METRIC = "set-up and solve time against N (icospheres at ~10 edges per wavelength)"
+
+
+def run_scaling(args):
+    """Set-up time, memory and solve time against N (the paper's scaling study,
+    Sec. IV, Eq. 46-56, Figs. 3 and 5) on icospheres of increasing level at a
+    fixed density: level L has radius 0.5 * 2^(L-3) wavelengths (level 5 is the
+    2 lambda benchmark sphere), leaf cap 128, ACA 1e-4, nested-dissection
+    order, reading A.  Per level: H-matrix build and scaling on the GPU (wall
+    time), device bytes, and the device time of the mixed solve (362-RHS sweep
+    and one RHS) and of the plain FP64 series (362 RHS and one RHS)."""
+    import numpy as np
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from hm_workloads import icosphere, monostatic_angles
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    th, ph, po = monostatic_angles("theta", 0.0, 180.0, 1.0, 0.0, (0, 1))
+    rows = []
+
+    def timed(sol, B, steps):
+        X = torch.empty_like(B)
+        sol.solve(X, B)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sol.solve(X, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps
+
+    for L in args.levels:
+        v, f = icosphere(L, 0.5 * 2 ** (L - 3))
+        row = {"level": L, "radius_lambda": 0.5 * 2 ** (L - 3)}
+        for prec in (hp.HM_MIXED, hp.HM_FP64):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol = hp.Solver.build(v, f, leaf_max=128, aca_tol=1e-4, ordering=hp.HM_ORDER_ND,
+                                  precision=prec, refine_steps=1 if prec == hp.HM_MIXED else 0)
+            t_build = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            sol.compute_scaling()
+            t_scale = time.perf_counter() - t0
+            B = torch.empty((len(th), sol.N), dtype=torch.complex128, device=dev)
+            sol.plane_wave(B, th, ph, po)
+            t_many = timed(sol, B, max(2, args.steps // 2))
+            t_one = timed(sol, B[:1].contiguous(), max(3, args.steps))
+            st = sol.stats()
+            tag = "mixed" if prec == hp.HM_MIXED else "fp64"
+            row.update({"N": sol.N, "leaves": st["leaves"], "alpha_entries": st["alpha_entries"],
+                        "near_entries": st["near_entries"], "far_entries": st["far_entries"],
+                        f"{tag}_build_s": round(t_build, 2), f"{tag}_scaling_s": round(t_scale, 2),
+                        f"{tag}_device_gb": round(st["device_bytes"] / 1e9, 2),
+                        f"{tag}_ms_362rhs": round(1e3 * t_many, 3),
+                        f"{tag}_rhs_per_s_362": round(len(th) / t_many, 1),
+                        f"{tag}_ms_1rhs": round(1e3 * t_one, 3)})
+            del sol, B
+            torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps({"partial": row}), file=sys.stderr, flush=True)
+    line = {"metric": SCALING_METRIC, "value": rows[-1]["mixed_rhs_per_s_362"], "unit": "RHS/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mixed and c128", "data": "synthetic",
+            "config": {"workload": "icospheres L" + ",".join(str(L) for L in args.levels) +
+                       ", radius 0.5*2^(L-3) lambda, leaves<=128, ACA 1e-4, ND order, "
+                       "reading A, 362 monostatic RHS and one RHS",
+                       "value_is": "mixed RHS/s at the largest level"},
+            "levels": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batch_accuracy(sols, Xs, Bs, ws_list, bar=1e-4):
+    """Each scatterer's grouped mixed result against the FP64 chain with the
+    same refinement on the same set-up: the mixed handle is saved (H-matrix,
+    scaling and supernodes, FP64 values) and loaded as an FP64 handle, one
+    scatterer at a time.  Returns the largest relative L2 error over all RHS
+    and the scatterers whose error exceeds the bar."""
+    import tempfile
+    import numpy as np
+    import torch
+    import paper_2109_04129_gb300 as hp
+    worst, over, per = 0.0, [], []
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "s.hmps")
+        for i, (sol, X, B) in enumerate(zip(sols, Xs, Bs)):
+            sol.save(path)
+            ref = hp.Solver.load(path, precision=hp.HM_FP64, refine_steps=1)
+            Xr = torch.empty_like(B)
+            ref.solve(Xr, B)
+            torch.cuda.synchronize()
+            e = float((torch.linalg.vector_norm(X - Xr, dim=1) /
+                       torch.linalg.vector_norm(Xr, dim=1)).max().item())
+            ratio = float(np.max(sol.diagnostics(B.shape[0])[0]))
+            per.append(round(e, 9))
+            worst = max(worst, e)
+            if e > bar:
+                over.append({"scatterer": ws_list[i].name, "N": sol.N, "rel_err": e,
+                             "series_ratio_max": ratio})
+            ref.close()
+            del Xr
+            os.unlink(path)
+    return {"rel_err_max": worst, "bar": bar, "over_bar": over, "per_scatterer": per,
+            "what": "grouped mixed solve vs FP64 chain + same refinement, same set-up"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sphere_scaling":
+        run_scaling(args)
     elif args.workload == "scatterer_batch":
         run_batch(args)
     else:

@@ -160,6 +160,111 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
   }
 }
 
+// One-RHS variant (nrhs == 1), bound by HBM bandwidth: every matrix entry is
+// read once and used once, so the kernel streams op(A) with coalesced loads
+// and keeps several loads in flight per thread.  One CTA (8 warps) per task,
+// output rows in chunks of 32:
+//   trans = 1 (op(A)[i][k] = A[k lda + i]): lane = output row, warp w takes
+//     the inner rows k = w, w + 8, ...: a warp reads 32 consecutive entries of
+//     one stored row, and x[k] is one broadcast load;
+//   trans = 0 (op(A)[i][k] = A[i lda + k]): warp w owns rows w, w + 8, w + 16,
+//     w + 24 of the chunk and its lanes walk k (coalesced along the stored
+//     row); each row's lane partials meet in a warp-shuffle reduction.
+// The eight warps' partials of a row are added in shared memory in warp
+// order (deterministic, no atomics).
+constexpr int GV_WARPS = 8;
+constexpr int GV_UNROLL = 4;
+template <class TA, class TV, class TC>
+__global__ void __launch_bounds__(256) k_gemv(const GTask* __restrict__ tasks,
+                                              const GItem* __restrict__ items, VBufs vb,
+                                              ABufs ab) {
+  const GTask t = tasks[blockIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ TC part[GV_WARPS][32];
+  typedef typename Cx<TC>::R R;
+  for (int r0 = 0; r0 < t.m; r0 += 32) {
+    const int mr = min(32, t.m - r0);
+    TC a1 = czero<TC>();            // trans = 1: row r0 + lane
+    TC a0[4];                       // trans = 0: rows r0 + w + 8q, this lane's share of k
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a0[q] = czero<TC>();
+    for (int it = t.it0; it < t.it1; ++it) {
+      const GItem I = items[it];
+      const TA* A = (const TA*)ab.p[I.a_buf] + I.a_off;
+      const TV* X = (const TV*)vb.p[I.in_buf] + I.in_row;
+      if (I.trans) {
+        if (lane < mr) {
+          const TA* Ai = A + r0 + lane;
+          int k = w;
+          for (; k + (GV_UNROLL - 1) * GV_WARPS < I.k; k += GV_UNROLL * GV_WARPS) {
+            TA av[GV_UNROLL];
+            TV xv[GV_UNROLL];
+#pragma unroll
+            for (int u = 0; u < GV_UNROLL; ++u) {
+              av[u] = Ai[(long long)(k + u * GV_WARPS) * I.lda];
+              xv[u] = X[k + u * GV_WARPS];
+            }
+#pragma unroll
+            for (int u = 0; u < GV_UNROLL; ++u) cmac(a1, cvt<TC, TA>(av[u]), cvt<TC, TV>(xv[u]));
+          }
+          for (; k < I.k; k += GV_WARPS)
+            cmac(a1, cvt<TC, TA>(Ai[(long long)k * I.lda]), cvt<TC, TV>(X[k]));
+        }
+      } else {
+        // the warp's four rows, their loads issued together
+        for (int k0 = 0; k0 < I.k; k0 += 32) {
+          const int k = k0 + lane;
+          TA av[4];
+          TV xv = k < I.k ? X[k] : TV{};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = w + 8 * q;
+            av[q] = (i < mr && k < I.k) ? A[(long long)(r0 + i) * I.lda + k] : TA{};
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cmac(a0[q], cvt<TC, TA>(av[q]), cvt<TC, TV>(xv));
+        }
+      }
+    }
+    // shuffle-reduce the trans = 0 partials of the warp's rows
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      R re = a0[q].x, im = a0[q].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      a0[q].x = re;
+      a0[q].y = im;
+    }
+    TC mine = a1;                    // this warp's partial of row r0 + lane
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (lane == w + 8 * q) {
+        mine.x += a0[q].x;
+        mine.y += a0[q].y;
+      }
+    part[w][lane] = mine;
+    __syncthreads();
+    if (w == 0 && lane < mr) {
+      TC v = part[0][lane];
+#pragma unroll
+      for (int q = 1; q < GV_WARPS; ++q) {
+        v.x += part[q][lane].x;
+        v.y += part[q][lane].y;
+      }
+      if (t.mode == 1) {
+        const TC b = cvt<TC, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + r0 + lane]);
+        v.x += b.x;
+        v.y += b.y;
+      }
+      ((TV*)vb.p[t.out_buf])[t.out_row + r0 + lane] = cvt<TV, TC>(v);
+    }
+    __syncthreads();
+  }
+}
+
 // Many-RHS variant: one CTA owns up to 128 rows of a target panel and a
 // 32-column RHS slice.  Lane = RHS column, warp = row group (rows g, g+8, ...),
 // so the inner dimension streams without row-tile padding: per inner index a
@@ -395,7 +500,7 @@ static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int 
                       cudaStream_t s) {
   int nt = (int)tl.tasks.size();
   if (nrhs == 1) {
-    k_gather_gemm<1, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
+    k_gemv<TA, TV, TC><<<nt, 256, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab);
   } else if (nrhs <= 4) {
     k_gather_gemm<4, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else if (nrhs <= 8) {

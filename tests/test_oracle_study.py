@@ -81,3 +81,48 @@ def test_mixed_error_model_small_case():
     es, ea = rel_err(xs, x64), rel_err(xa, x64)
     assert np.all(es > 0) and np.all(es < 1e-5)
     assert np.all(ea < 1e-4) and ea.max() > es.max()
+
+
+def test_binary_tree_partition():
+    """The paper's binary tree (study reading): leaves tile the points, every
+    leaf's longest edge lies in [leaf size, 2 leaf size), near and far blocks
+    tile the index square once, and every far pair meets Eq. 10 (checked on
+    the cell geometry, not with the tree's own test)."""
+    from hm_workloads import icosphere
+    from oracle.rwg import build_rwg
+    from oracle.study_leaf_size import BinaryTree, leaf_edges
+    v, f = icosphere(3, 1.0)
+    pts = build_rwg(v, f).centre
+    for size, eta in ((0.25, 1.0), (0.5, 1.0), (0.5, 2.0)):
+        T = BinaryTree(pts, size, eta)
+        assert sorted(T.perm.tolist()) == list(range(len(pts)))
+        e = leaf_edges(T, 1.0)
+        assert np.all(e >= size) and np.all(e < 2 * size)
+        for n in T.leaves:
+            nd = T.nodes[n]
+            p = pts[T.perm[nd.start:nd.start + nd.count]]
+            assert np.all(p >= nd.lo - 1e-12) and np.all(p <= nd.hi + 1e-12)
+        near, far = T.blocks()
+        cover = np.zeros((len(pts), len(pts)), np.int8)
+        for i, j in near:
+            cover[T.leaf_off[i]:T.leaf_off[i + 1], T.leaf_off[j]:T.leaf_off[j + 1]] += 1
+        for s, t in far:
+            a, b = T.nodes[s], T.nodes[t]
+            cover[a.start:a.start + a.count, b.start:b.start + b.count] += 1
+            # Eq. 10 on the cells: min diagonal <= eta * (distance between cells)
+            lo = np.maximum(a.lo, b.lo)
+            hi = np.minimum(a.hi, b.hi)
+            dist = np.linalg.norm(np.maximum(0.0, lo - hi))
+            dmin = min(np.linalg.norm(a.hi - a.lo), np.linalg.norm(b.hi - b.lo))
+            assert dist > 0 and dmin <= eta * dist + 1e-12
+        assert cover.min() == 1 and cover.max() == 1
+
+
+def test_leaf_size_study_binary_tree_runs():
+    r = subprocess.run([sys.executable, "-m", "oracle.study_leaf_size", "--level", "2",
+                        "--radius", "0.25", "--binary", "0.1", "1.0", "--terms", "2",
+                        "--processes", "1"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr
+    rows = [ln.split() for ln in r.stdout.splitlines() if not ln.startswith("#")]
+    assert len(rows) == 2 and int(rows[0][1]) > int(rows[1][1])
