@@ -30,10 +30,12 @@ METRIC = "power-series RHS solves/s at rel.err ≤1e-4 vs FP64; mixed vs FP64 on
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # FP64-accurate residual far-field kernels, from one ncu capture of this bench
 # (2-lambda sphere, 362 RHS, mixed precision; summary under profiles/).  They
-# are reported as the roofline's "traffic" only while the kernel's code (the
-# source with comments and whitespace removed) still hashes to the captured
-# version; any later change of the code turns them off (null).
-NCU_TRAFFIC_SOURCE = ("paper_2109_04129_gb300/csrc/hm_oz.cu",
+# are reported as the roofline's "traffic" only while the code of the kernel
+# and of the schedules it walks (the sources with comments and whitespace
+# removed) still hashes to the captured version; any later change turns them
+# off (null).
+NCU_TRAFFIC_SOURCE = (("paper_2109_04129_gb300/csrc/hm_oz.cu",
+                       "paper_2109_04129_gb300/csrc/hm_api.cu"),
                       "dc416b2e820988aca8d7d1348c338ccba5d1e667df201ff26e5a7c77588c8eaf")
 NCU_TRAFFIC = {("sphere_r2_L5", "mixed", 362, "far_stage1"): 2.230756e9 + 1.990304e9,
                ("sphere_r2_L5", "mixed", 362, "far_stage2"): 30.976054e9 + 0.187359e9}
@@ -55,9 +57,12 @@ def captured_traffic(workload, precision, nrhs, kernel):
     b = NCU_TRAFFIC.get((workload, precision, nrhs, kernel))
     if b is None:
         return None
-    with open(os.path.join(ROOT, NCU_TRAFFIC_SOURCE[0])) as f:
-        if code_hash(f.read()) != NCU_TRAFFIC_SOURCE[1]:
-            return None
+    text = ""
+    for path in NCU_TRAFFIC_SOURCE[0]:
+        with open(os.path.join(ROOT, path)) as f:
+            text += f.read()
+    if code_hash(text) != NCU_TRAFFIC_SOURCE[1]:
+        return None
     return b
 
 
@@ -76,6 +81,12 @@ def parse():
     ap.add_argument("--no-single-rhs", action="store_true",
                     help="skip the one-RHS (bandwidth-bound) leg")
     ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
+    ap.add_argument("--chunk", type=int, default=120,
+                    help="RHS per call of --workload sphere_r10_L7")
+    ap.add_argument("--fill", default="B", choices=["A", "B"],
+                    help="scaling reading of --workload sphere_r10_L7")
+    ap.add_argument("--oracle-check", action="store_true",
+                    help="sphere_r10_L7: oracle series on the library's blocks (8 RHS)")
     ap.add_argument("--levels", type=int, nargs="+", default=[3, 4, 5, 6],
                     help="icosphere levels of --workload sphere_scaling")
     ap.add_argument("--batch-count", type=int, default=64,
@@ -975,10 +986,155 @@ def batch_accuracy(sols, Xs, Bs, ws_list, bar=1e-4):
             "what": "grouped mixed solve vs FP64 chain + same refinement, same set-up"}
 
 
+# ------------------------------------------------------- the 10 lambda sphere (RHS in chunks)
+def run_large(args):
+    """The 10 lambda sphere (icosphere level 7, N = 491520, leaves <= 256, ACA
+    1e-4, 720 monostatic RHS theta = 0..179.75 step 0.25): H-matrix fill and
+    scaling on the GPU, then the mixed series with one refinement over the
+    720 RHS in chunks of --chunk RHS per call (the stage-1 far-field panels
+    grow as 2 (sum of far ranks) x nrhs, which bounds one call's batch on one
+    GPU).  Accuracy on the 8 sampled RHS 0, 90, ..., 630: against the library's
+    FP64 chain with the same refinement on the same set-up (the mixed handle
+    saved and loaded as FP64) and, with --oracle-check, against the CPU
+    oracle's series + refinement on the library's own blocks (imported), which
+    also gives the CPU baseline."""
+    import tempfile
+    import numpy as np
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from hm_workloads import get_workload
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    w = get_workload(args.workload)
+    v, f = w.build_mesh()
+    fill = hp.HM_FILL_NEAR if args.fill == "B" else hp.HM_FILL_FULL
+    t0 = time.perf_counter()
+    sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max, aca_tol=w.aca_tol,
+                          ordering=hp.HM_ORDER_ND, fill=fill, precision=hp.HM_MIXED,
+                          refine_steps=1)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sol.compute_scaling()
+    t_scale = time.perf_counter() - t0
+    st = sol.stats()
+    th, ph, po = w.angles()
+    nrhs = len(th)
+    B = torch.empty((nrhs, sol.N), dtype=torch.complex128, device=dev)
+    sol.plane_wave(B, th, ph, po)
+    X = torch.empty_like(B)
+    c = max(1, min(args.chunk, nrhs))
+    chunks = [(r, min(nrhs, r + c)) for r in range(0, nrhs, c)]
+
+    def sweep():
+        for a, b in chunks:
+            sol.solve(X[a:b], B[a:b])
+
+    sol.solve(X[:c], B[:c])                     # sizes the work panels
+    torch.cuda.synchronize()
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    for _ in range(max(0, args.warmup - 1)):
+        sweep()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = sol.stats()["kernel_launches"]
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            sweep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = sol.stats()["kernel_launches"] - l0
+    t_dev = e0.elapsed_time(e1) / 1e3 / args.steps
+    ratio = np.concatenate([sol.diagnostics(b - a)[0] for a, b in chunks[-1:]])
+    sol.profile_enable(True)
+    sol.solve(X[:c], B[:c])
+    prof = sol.profile()
+    sol.profile_enable(False)
+    peaks, peak_kind = measured_peaks()
+    roof = roofline(prof, c, True, peaks, peak_kind, dev)
+    # end to end: pinned host chunks in and out through the host-buffer call
+    Bh = torch.empty((nrhs, sol.N), dtype=torch.complex128, pin_memory=True)
+    Bh.copy_(B)
+    Xh = torch.empty_like(Bh, pin_memory=True)
+    bn, xn = Bh.numpy(), Xh.numpy()
+    t0 = time.perf_counter()
+    for a, b in chunks:
+        sol.solve_host(xn[a:b], bn[a:b])
+    t_e2e = time.perf_counter() - t0
+    idx = list(range(0, nrhs, 90))[:8]
+    xm = X[idx].cpu().numpy().T.copy()
+    bs = B[idx].cpu().numpy().T.copy()
+    acc = {"sampled_rhs": idx}
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "s10.hmps")
+        sol.save(path)
+        del sol, X, Bh, Xh
+        torch.cuda.empty_cache()
+        ref = hp.Solver.load(path, precision=hp.HM_FP64, refine_steps=1)
+        Bs = torch.from_numpy(np.ascontiguousarray(bs.T)).to(dev)
+        Xr = torch.empty_like(Bs)
+        ref.solve(Xr, Bs)
+        x64 = Xr.cpu().numpy().T
+        e = np.linalg.norm(xm - x64, axis=0) / np.linalg.norm(x64, axis=0)
+        acc["mixed_vs_gpu_fp64_refined_rel_err"] = [float(x) for x in e]
+        ref.close()
+        cpu = None
+        if args.oracle_check:
+            from oracle.export import load_blocks
+            from oracle.series import refine_once, series_solve
+            H, S = load_blocks(path)
+            t0 = time.perf_counter()
+            x2, _ = series_solve(H, S, bs, 2)
+            xo = refine_once(H, S, bs, x2)
+            t_or = time.perf_counter() - t0
+            acc["mixed_vs_oracle_rel_err"] = [
+                float(x) for x in np.linalg.norm(xm - xo, axis=0) / np.linalg.norm(xo, axis=0)]
+            acc["gpu_fp64_vs_oracle_rel_err"] = [
+                float(x) for x in np.linalg.norm(x64 - xo, axis=0) / np.linalg.norm(xo, axis=0)]
+            cpu = {"value": len(idx) / t_or, "unit": "RHS/s", "cores": cpu_threads(),
+                   "kind": "oracle",
+                   "sample": f"the {len(idx)} sampled RHS, oracle FP64 series + one refinement "
+                             "step on the library's blocks (imported), one run"}
+    acc["bar"] = 1e-4
+    line = {
+        "metric": METRIC, "value": nrhs / t_dev, "unit": "RHS/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: c64 chain on tcgen05 (3-way bf16 split, f32 accum), c128 D^-1, "
+                 "FP64-accurate residual on tcgen05 (exact 7-bit slicing)",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(w, st["N"], nrhs),
+                   "precision": "mixed", "ordering": "nd",
+                   "fill": "reading B (near-pattern fill)" if fill == hp.HM_FILL_NEAR
+                           else "reading A (full fill)",
+                   "rhs_per_call": c, "calls_per_step": len(chunks),
+                   "l2": "inputs larger than L2, no flush", "parallelism": "single GPU",
+                   "alpha_entries": st["alpha_entries"], "far_entries": st["far_entries"],
+                   "near_entries": st["near_entries"], "leaves": st["leaves"],
+                   "build_s": round(t_build, 1), "scaling_s": round(t_scale, 1),
+                   "device_gb_held": round(st["device_bytes"] / 1e9, 1),
+                   "device_gb_free_after_first_solve": round(free_b / 1e9, 1),
+                   "series_ratio_max_last_chunk": float(np.max(ratio))},
+        "roofline": roof, "accuracy": acc,
+        "e2e": {"value": nrhs / t_e2e, "unit": "RHS/s", "h2d_bytes_per_step": int(bn.nbytes),
+                "d2h_bytes_per_step": int(xn.nbytes)},
+        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernel_table(prof, 1),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sphere_r10_L7":
+        run_large(args)
     elif args.workload == "sphere_scaling":
         run_scaling(args)
     elif args.workload == "scatterer_batch":

@@ -96,8 +96,11 @@ def write_blocks(path, H, S=None, centres=True, groups=None):
 
 
 def read_blocks(path):
-    """Inverse of write_blocks -> dict of numpy arrays (tests only)."""
-    buf = open(path, "rb").read()
+    """Inverse of write_blocks -> dict of numpy arrays (tests only).  The file
+    is memory-mapped: the arrays are read-only views of it."""
+    import mmap
+    with open(path, "rb") as fh:
+        buf = mmap.mmap(fh.fileno(), 0, access=mmap.ACCESS_READ)
     assert buf[:8] == MAGIC
     pos = 8
 
@@ -167,3 +170,22 @@ def read_blocks(path):
             raise ValueError(f"unknown section {tag!r}")
     assert pos == len(buf)
     return out
+
+
+def load_blocks(path):
+    """(H, S) of the oracle from a block file written by the GPU library
+    (hm_save): its H-matrix and, when present, its scaling coefficients, so
+    that the oracle's series can check the library on the library's own
+    blocks ("imported blocks").  S.D is not in the file (None)."""
+    from .hmatrix import HMatrix
+    from .scaling import Scaling
+    d = read_blocks(path)
+    H = HMatrix(N=int(d["N"]), perm=np.asarray(d["perm"]), leaf_off=np.asarray(d["leaf_off"]),
+                near=d["near"], far=d["far"], k=float(d["k"]),
+                meta={"wavelength": float(d["wavelength"])})
+    S = None
+    if "alpha" in d:
+        S = Scaling(n=len(d["elim"]), rows=d["rows"], alpha=d["alpha"], D=None,
+                    Dinv=d["Dinv"], reading="A" if d["reading"] == 0 else "B",
+                    order=d["elim"])
+    return H, S

@@ -389,6 +389,42 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
   sw.scratch_rows = max_scr;
 }
 
+// Tasks of more than mmax output rows become row slices of at most mmax rows
+// with the same items (matrix reads offset by the slice's first row; a
+// split-K slice writes its rows of the target's partial panel).  The
+// tensor-core engine takes at most 128 complex rows per task (MMA N = 256);
+// leaves of up to 256 unknowns (leaf cap 256) would otherwise send a whole
+// launch to the CUDA-core kernels.  Each output row keeps its items and inner
+// order, so the arithmetic of every row is unchanged.
+void split_wide_tasks(TaskList& tl, int mmax) {
+  bool any = false;
+  for (const GTask& t : tl.tasks) any |= (t.m > mmax && t.mode != 2);
+  if (!any) return;
+  std::vector<GTask> nt;
+  std::vector<GItem> ni;
+  for (const GTask& t : tl.tasks) {
+    const int step = (t.mode == 2) ? std::max(1, t.m) : mmax;
+    for (int r = 0; r < std::max(1, t.m); r += step) {
+      GTask sl = t;
+      if (t.mode != 2) {
+        sl.m = std::min(step, t.m - r);
+        sl.out_row = t.out_row + r;
+        if (t.mode == 1) sl.base_row = t.base_row + r;
+      }
+      sl.it0 = (int)ni.size();
+      for (int q = t.it0; q < t.it1; ++q) {
+        GItem I = tl.items[q];
+        if (t.mode != 2) I.a_off += I.trans ? (long long)r : (long long)r * I.lda;
+        ni.push_back(I);
+      }
+      sl.it1 = (int)ni.size();
+      nt.push_back(sl);
+    }
+  }
+  tl.tasks.swap(nt);
+  tl.items.swap(ni);
+}
+
 bool has_groups(hm_ctx* h) {
   for (int x : h->tg_n)
     if (x) return true;
@@ -420,6 +456,8 @@ hm_status build_schedules(hm_ctx* h) {
       build_sweep(h, true, h->fwd);
       build_sweep(h, false, h->bwd);
     }
+    for (Sweep* sw : {&h->fwd, &h->bwd})
+      for (TaskList& tl : sw->part) split_wide_tasks(tl, 128);
     for (int q = 0; q < n; ++q) {
       const int k = h->elim[q];
       GTask t{VB_OUT, (int)h->leaf_off[k], h->m[k], (int)h->dinv_tl.items.size(), 0, 0, 0, 0};
@@ -483,6 +521,7 @@ hm_status build_schedules(hm_ctx* h) {
   h->far1s_tl.a_bytes = h->far1_tl.a_bytes;
   h->far_t_rows = nt;
   std::vector<std::vector<GItem>> per_leaf(n);
+  std::vector<std::vector<int>> share(n);      // per item: unknowns of its cluster
   auto leaf_of = [&](long long row) {
     return (int)(std::upper_bound(h->leaf_off.begin(), h->leaf_off.end(), row) -
                  h->leaf_off.begin()) - 1;
@@ -498,6 +537,7 @@ hm_status build_schedules(hm_ctx* h) {
       } else {
         per_leaf[l].push_back(GItem{f.offU + dr * f.n, AB_FAR, f.n, 0, f.n, VB_IN, f.c0});
       }
+      share[l].push_back(f.m);
     }
     for (int l = leaf_of(f.c0); l < n && h->leaf_off[l] < f.c0 + f.n; ++l) {
       long long dc = h->leaf_off[l] - f.c0;
@@ -508,14 +548,31 @@ hm_status build_schedules(hm_ctx* h) {
       } else {
         per_leaf[l].push_back(GItem{f.offU + dc, AB_FAR, f.n, 1, f.m, VB_IN, f.r0});
       }
+      share[l].push_back(f.n);
     }
   }
   for (int l = 0; l < n; ++l) {
     GTask t{VB_OUT, (int)h->leaf_off[l], h->m[l], (int)h->far2_tl.items.size(), 0, 0, 0, 0};
-    // stage-1 panel items first, then the dense blocks on the input: the
-    // FP64-accurate engine changes its input scale at most once per task
-    std::stable_partition(per_leaf[l].begin(), per_leaf[l].end(),
-                          [](const GItem& it) { return it.in_buf == VB_FAR; });
+    // stage-1 panel items first, then the dense blocks on the input (the
+    // FP64-accurate engine changes its input scale at most once per task);
+    // the stage-1 items of the largest clusters lead, in stage-1 row order:
+    // every leaf of a cluster reads those same rows, and the leaves that run
+    // side by side (neighbouring work units) then reach them at about the same
+    // time, while the rows are still in L2
+    std::vector<int> ord(per_leaf[l].size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+    const std::vector<GItem>& pl = per_leaf[l];
+    const std::vector<int>& sh = share[l];
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const bool fa = pl[a].in_buf == VB_FAR, fb = pl[b].in_buf == VB_FAR;
+      if (fa != fb) return fa;
+      if (!fa) return false;
+      if (sh[a] != sh[b]) return sh[a] > sh[b];
+      return pl[a].in_row < pl[b].in_row;
+    });
+    std::vector<GItem> sorted;
+    for (int q : ord) sorted.push_back(pl[q]);
+    per_leaf[l].swap(sorted);
     for (auto& it : per_leaf[l]) {
       h->far2_tl.items.push_back(it);
       h->far2_tl.flops += (long long)h->m[l] * it.k;
@@ -524,6 +581,7 @@ hm_status build_schedules(hm_ctx* h) {
     t.it1 = (int)h->far2_tl.items.size();
     h->far2_tl.tasks.push_back(t);
   }
+  split_wide_tasks(h->far2_tl, 128);
   // near field Z_N (upper blocks + transposes)
   std::vector<std::vector<GItem>> near_leaf(n);
   for (const NearDesc& d : h->near) {
@@ -668,7 +726,11 @@ hm_status ensure_err(hm_ctx* h) {
 // launched by the callers that hold split panels of the inputs)
 static hm_status launch_any(hm_ctx* h, const TaskList& tl, const VBufs& v, const ABufs& a,
                             int nrhs, int prec) {
-  return launch_tasks(tl, v, a, nrhs, h->stream, prec);
+  if (nrhs == 1) {                      // the one-RHS kernels wait on copy barriers
+    hm_status s = ensure_err(h);
+    if (s) return s;
+  }
+  return launch_tasks(tl, v, a, nrhs, h->stream, prec, h->p.spin_limit, h->d_err);
 }
 
 hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs, int cat,

@@ -76,6 +76,8 @@ struct TaskList {
   // FP64-accurate path: work units (task, 32-row pass), costliest first
   int2* d_units = nullptr;
   int n_units = 0;
+  // one-RHS bulk-copy kernel usable for this list (-1: not checked yet)
+  mutable int bulk_ok = -1;
 };
 // per-task row scale exponents of a task list (FP64-accurate tensor products)
 struct RowExp {
@@ -189,7 +191,8 @@ struct hm_ctx {
 namespace hm {
 // kernels.cu
 hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                       cudaStream_t s, int prec = PREC_64);
+                       cudaStream_t s, int prec = PREC_64, long long spin_limit = 1LL << 26,
+                       int* err = nullptr);
 hm_status launch_fin(const FinList& fl, const VBufs& vb, int nrhs, cudaStream_t s,
                      int prec = PREC_64);
 hm_status launch_gather_perm32(const cplx* B, float2* V, const int* perm, int N, int nrhs,

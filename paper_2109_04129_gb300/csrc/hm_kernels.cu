@@ -7,6 +7,8 @@
 // Layout: vector panels are row-major (row stride nrhs, RHS fastest), so a
 // row of a panel is one contiguous run of complex values.  Matrix blocks are
 // row-major complex128.
+#include <type_traits>
+
 #include "hm_internal.h"
 
 namespace hm {
@@ -265,6 +267,211 @@ __global__ void __launch_bounds__(256) k_gemv(const GTask* __restrict__ tasks,
   }
 }
 
+// One-RHS variant for complex128 matrices with the blocks staged by bulk
+// copies.  Every item of a task is a set of stored rows of one matrix block:
+// trans = 0: rows i < m, each k entries (op(A)[i][kk] = A[i lda + kk]);
+// trans = 1: rows kk < k, each m entries (op(A)[i][kk] = A[kk lda + i]).
+// A piece is a run of whole stored rows of one item, at most GB_CHUNK bytes;
+// warp 8 (one thread) copies the pieces in order into a ring of GB_STAGES
+// shared-memory stages (cp.async.bulk, completion on the stage's "full"
+// mbarrier: one copy when the rows are contiguous, else one per row), and the
+// eight consumer warps multiply them as they land ("empty" mbarrier, eight
+// arrivals, hands the stage back), so several pieces are in flight per CTA.
+//   trans = 1: thread c is row i = c % m of group c / m; group g takes the
+//     stored rows kk = g, g + G, ... of each piece (G = 256 / m groups);
+//   trans = 0: warp w takes the rows i = w mod 8 of each piece, lanes along
+//     kk, one warp-shuffle reduction per row into a shared row sum.
+// Rows are added in a fixed order (deterministic).  Every wait is bounded: a
+// CTA that gives up records it in *err, waits (bounded) for its own copies in
+// flight and leaves its outputs unwritten.  Tasks of at most 256 rows and
+// stored rows of at most GB_CHUNK bytes (checked on the host per list).
+constexpr int GB_STAGES = 4;
+constexpr int GB_CHUNK = 16384;
+constexpr int GB_THREADS = 288;           // 8 consumer warps + 1 copy warp
+constexpr int GB_SMEM = GB_STAGES * GB_CHUNK + 1024;
+
+__device__ __forceinline__ bool gb_wait(uint32_t bar, uint32_t phase, long long limit,
+                                        volatile int* abort_flag, int* err) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase));
+    if (done) return true;
+    if (abort_flag && *abort_flag) return false;
+  }
+  if (abort_flag) *abort_flag = 1;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
+// stored rows of item I and the entries of each (see k_gemv_bulk)
+__device__ __forceinline__ void gb_rows(const GItem& I, int m, int& nrow, int& len) {
+  nrow = I.trans ? I.k : m;
+  len = I.trans ? m : I.k;
+}
+
+template <class TV>
+__global__ void __launch_bounds__(GB_THREADS) k_gemv_bulk(const GTask* __restrict__ tasks,
+                                                          const GItem* __restrict__ items,
+                                                          VBufs vb, ABufs ab,
+                                                          long long spin_limit, int* err) {
+  extern __shared__ __align__(128) unsigned char gb_smem[];
+  __shared__ __align__(8) uint64_t bars[2 * GB_STAGES];
+  __shared__ double2 part[256];            // trans = 1 partials [group][row]
+  __shared__ double2 rowsum[256];          // trans = 0 row sums
+  __shared__ int abort_flag, issued_s;
+  const GTask t = tasks[blockIdx.x];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const uint32_t b_full = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+  const uint32_t b_empty = (uint32_t)__cvta_generic_to_shared(&bars[GB_STAGES]);
+  volatile int* abortp = &abort_flag;
+  const int m = t.m;
+  if (tid == 0) {
+    for (int b = 0; b < GB_STAGES; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b_full + 8u * b));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" :: "r"(b_empty + 8u * b));
+    }
+    abort_flag = 0;
+    issued_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  for (int e = tid; e < 256; e += GB_THREADS) {
+    part[e] = make_double2(0.0, 0.0);
+    rowsum[e] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  if (w == 8) {
+    // ------------------------------------------------ copies (one thread)
+    if (lane == 0) {
+      int g = 0;
+      bool stop = false;
+      for (int it = t.it0; it < t.it1 && !stop; ++it) {
+        const GItem I = items[it];
+        int nrow, len;
+        gb_rows(I, m, nrow, len);
+        const int rb = len * 16;
+        const int per = max(1, GB_CHUNK / rb);
+        const unsigned char* A = (const unsigned char*)((const double2*)ab.p[I.a_buf] + I.a_off);
+        const bool contig = I.lda == len;
+        for (int r = 0; r < nrow; r += per) {
+          const int nr = min(per, nrow - r);
+          const int b = g % GB_STAGES;
+          if (g >= GB_STAGES &&
+              !gb_wait(b_empty + 8u * b, (uint32_t)(((g - GB_STAGES) / GB_STAGES) & 1), spin_limit,
+                       abortp, err)) {
+            stop = true;
+            break;
+          }
+          const uint32_t fb = b_full + 8u * b;
+          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(gb_smem + b * GB_CHUNK);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                       :: "r"(fb), "r"(nr * rb) : "memory");
+          if (contig) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                :: "r"(dst), "l"(A + (long long)r * rb), "r"(nr * rb), "r"(fb) : "memory");
+          } else {
+            for (int q = 0; q < nr; ++q)
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                  :: "r"(dst + (uint32_t)(q * rb)), "l"(A + (long long)(r + q) * I.lda * 16),
+                     "r"(rb), "r"(fb) : "memory");
+          }
+          ++g;
+          issued_s = g;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ consumers (8 warps)
+    const int G = m > 0 ? max(1, 256 / m) : 1;
+    const int grp = tid / max(1, m), row = tid % max(1, m);
+    const bool t1 = m > 0 && grp < G;       // this thread owns (group, row) for trans = 1
+    double2 acc1 = make_double2(0.0, 0.0);
+    int g = 0;
+    bool stop = false;
+    for (int it = t.it0; it < t.it1 && !stop; ++it) {
+      const GItem I = items[it];
+      int nrow, len;
+      gb_rows(I, m, nrow, len);
+      const int per = max(1, GB_CHUNK / (len * 16));
+      const TV* X = (const TV*)vb.p[I.in_buf] + I.in_row;
+      for (int r = 0; r < nrow; r += per) {
+        const int nr = min(per, nrow - r);
+        const int b = g % GB_STAGES;
+        // one decision per warp
+        bool ok = true;
+        if (lane == 0) ok = gb_wait(b_full + 8u * b, (uint32_t)((g / GB_STAGES) & 1), spin_limit,
+                                    abortp, err);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+          stop = true;
+          break;
+        }
+        const double2* S = (const double2*)(gb_smem + b * GB_CHUNK);
+        if (I.trans) {
+          if (t1)
+            for (int q = grp; q < nr; q += G) {
+              const double2 a = S[q * len + row];
+              cmac(acc1, a, cvt<double2, TV>(X[r + q]));
+            }
+        } else {
+          for (int q = (w - r % 8 + 8) % 8; q < nr; q += 8) {   // rows i = r + q with i % 8 == w
+            double2 v = make_double2(0.0, 0.0);
+            for (int kk = lane; kk < len; kk += 32)
+              cmac(v, S[q * len + kk], cvt<double2, TV>(X[kk]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+              v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            }
+            if (lane == 0) {
+              double2& rs = rowsum[r + q];
+              rs.x += v.x;
+              rs.y += v.y;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b_empty + 8u * b) : "memory");
+        ++g;
+      }
+    }
+    if (t1) part[tid] = acc1;
+  }
+  __syncthreads();
+  if (abort_flag) {
+    // the copies still in flight (at most the last GB_STAGES issued, the
+    // latest phase of each stage barrier) land before the CTA leaves
+    if (tid == 0) {
+      volatile int never = 0;
+      const long long lim = spin_limit > (1LL << 24) ? spin_limit : (1LL << 24);
+      for (int g = max(0, issued_s - GB_STAGES); g < issued_s; ++g)
+        gb_wait(b_full + 8u * (g % GB_STAGES), (uint32_t)((g / GB_STAGES) & 1), lim, &never,
+                nullptr);
+    }
+    __syncthreads();
+    return;
+  }
+  if (tid < m) {
+    const int G = max(1, 256 / m);
+    double2 v = rowsum[tid];
+    for (int q = 0; q < G; ++q) {
+      const double2 p = part[q * m + tid];
+      v.x += p.x;
+      v.y += p.y;
+    }
+    if (t.mode == 1) {
+      const double2 bv = cvt<double2, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + tid]);
+      v.x += bv.x;
+      v.y += bv.y;
+    }
+    ((TV*)vb.p[t.out_buf])[t.out_row + tid] = cvt<TV, double2>(v);
+  }
+}
+
 // Many-RHS variant: one CTA owns up to 128 rows of a target panel and a
 // 32-column RHS slice.  Lane = RHS column, warp = row group (rows g, g+8, ...),
 // so the inner dimension streams without row-tile padding: per inner index a
@@ -495,12 +702,35 @@ int grid_for(long long n) {
 
 }  // namespace
 
+// the bulk-copy kernel takes the list: tasks of at most 256 rows, every stored
+// row of an item at most GB_CHUNK bytes, no stacked tasks
+static bool bulk_ok_for(const TaskList& tl) {
+  if (tl.bulk_ok < 0) {
+    bool ok = true;
+    for (const GTask& t : tl.tasks) {
+      if (t.mode == 2 || t.m > 256) { ok = false; break; }
+      for (int q = t.it0; q < t.it1 && ok; ++q) {
+        const GItem& I = tl.items[q];
+        const int len = I.trans ? t.m : I.k;
+        if (len * 16 > GB_CHUNK || len <= 0 || I.lda < len) ok = false;
+      }
+      if (!ok) break;
+    }
+    tl.bulk_ok = ok ? 1 : 0;
+  }
+  return tl.bulk_ok == 1;
+}
+
 template <class TA, class TV, class TC>
 static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                      cudaStream_t s) {
+                      cudaStream_t s, long long spin_limit, int* err) {
   int nt = (int)tl.tasks.size();
   if (nrhs == 1) {
-    k_gemv<TA, TV, TC><<<nt, 256, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab);
+    if (std::is_same<TA, double2>::value && err && bulk_ok_for(tl))
+      k_gemv_bulk<TV><<<nt, GB_THREADS, GB_SMEM, s>>>(tl.d_tasks, tl.d_items, vb, ab,
+                                                       spin_limit, err);
+    else
+      k_gemv<TA, TV, TC><<<nt, 256, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab);
   } else if (nrhs <= 4) {
     k_gather_gemm<4, TA, TV, TC><<<dim3(nt, 1), NTHR, 0, s>>>(tl.d_tasks, tl.d_items, vb, ab, nrhs);
   } else if (nrhs <= 8) {
@@ -512,14 +742,22 @@ static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int 
 }
 
 hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
-                       cudaStream_t s, int prec) {
+                       cudaStream_t s, int prec, long long spin_limit, int* err) {
   if (tl.tasks.empty()) return HM_OK;
+  static bool attr = false;
+  if (!attr) {
+    HM_CUDA(cudaFuncSetAttribute(k_gemv_bulk<double2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GB_SMEM));
+    HM_CUDA(cudaFuncSetAttribute(k_gemv_bulk<float2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GB_SMEM));
+    attr = true;
+  }
   if (prec == PREC_64)
-    launch_tl<double2, double2, double2>(tl, vb, ab, nrhs, s);
+    launch_tl<double2, double2, double2>(tl, vb, ab, nrhs, s, spin_limit, err);
   else if (prec == PREC_32)
-    launch_tl<float2, float2, float2>(tl, vb, ab, nrhs, s);
+    launch_tl<float2, float2, float2>(tl, vb, ab, nrhs, s, spin_limit, err);
   else
-    launch_tl<double2, float2, double2>(tl, vb, ab, nrhs, s);
+    launch_tl<double2, float2, double2>(tl, vb, ab, nrhs, s, spin_limit, err);
   HM_LAUNCHED();
   return HM_OK;
 }

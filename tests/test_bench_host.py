@@ -48,8 +48,11 @@ def test_captured_traffic_gated_on_source(monkeypatch):
     key = ("sphere_r2_L5", "mixed", 362, "far_stage2")
     assert key in bench.NCU_TRAFFIC
     # a source whose code hashes to the recorded value reports the captured figure
-    with open(os.path.join(ROOT, bench.NCU_TRAFFIC_SOURCE[0])) as f:
-        now = bench.code_hash(f.read())
+    text = ""
+    for path in bench.NCU_TRAFFIC_SOURCE[0]:
+        with open(os.path.join(ROOT, path)) as f:
+            text += f.read()
+    now = bench.code_hash(text)
     monkeypatch.setattr(bench, "NCU_TRAFFIC_SOURCE", (bench.NCU_TRAFFIC_SOURCE[0], now))
     assert bench.captured_traffic(*key) == bench.NCU_TRAFFIC[key]
     # not captured: other kernel, precision or RHS count

@@ -142,3 +142,24 @@ def test_block_file_sections_round_trip():
     for g, T in d["T"].items():
         assert np.array_equal(T, supernode_inverse(S, H.leaf_off, groups[g], groups[g + 1]))
     assert len(d["T"]) == int((np.diff(groups) > 1).sum())
+
+
+def test_load_blocks_gives_the_same_series():
+    """The oracle's loader of block files (used to check the library on its
+    own blocks) reproduces the series of the H-matrix and scaling it was
+    written from."""
+    from oracle.export import load_blocks
+    from oracle.series import series_solve
+    H, S, order, groups = _nd_case()
+    fd, path = tempfile.mkstemp(suffix=".hmps")
+    os.close(fd)
+    try:
+        write_blocks(path, H, S)
+        H2, S2 = load_blocks(path)
+        rng = np.random.default_rng(2)
+        b = rng.standard_normal((H.N, 2)) + 1j * rng.standard_normal((H.N, 2))
+        x1, r1 = series_solve(H, S, b, 3)
+        x2, r2 = series_solve(H2, S2, b, 3)
+        assert np.array_equal(x1, x2) and np.array_equal(r1, r2)
+    finally:
+        os.unlink(path)
