@@ -165,72 +165,89 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
 // One-RHS variant (nrhs == 1), bound by HBM bandwidth: every matrix entry is
 // read once and used once, so the kernel streams op(A) with coalesced loads
 // and keeps several loads in flight per thread.  One CTA (8 warps) per task,
-// output rows in chunks of 32:
-//   trans = 1 (op(A)[i][k] = A[k lda + i]): lane = output row, warp w takes
-//     the inner rows k = w, w + 8, ...: a warp reads 32 consecutive entries of
-//     one stored row, and x[k] is one broadcast load;
-//   trans = 0 (op(A)[i][k] = A[i lda + k]): warp w owns rows w, w + 8, w + 16,
-//     w + 24 of the chunk and its lanes walk k (coalesced along the stored
-//     row); each row's lane partials meet in a warp-shuffle reduction.
-// The eight warps' partials of a row are added in shared memory in warp
-// order (deterministic, no atomics).
+// output rows in chunks of 64:
+//   trans = 1 (op(A)[i][k] = A[k lda + i]): lane = output rows (lane and
+//     lane + 32), warp w takes the inner rows k = w, w + 8, ...: a warp reads
+//     consecutive entries of one stored row, and x[k] is one broadcast load;
+//   trans = 0 (op(A)[i][k] = A[i lda + k]): warp w owns rows w, w + 8, ...,
+//     w + 56 of the chunk and its lanes walk k (coalesced along the stored
+//     rows, the eight rows' loads issued together); each row's lane partials
+//     meet in a warp-shuffle reduction.
+// The next item's descriptor is fetched while the current one streams.  The
+// eight warps' partials of a row are added in shared memory in warp order
+// (deterministic, no atomics).
 constexpr int GV_WARPS = 8;
 constexpr int GV_UNROLL = 4;
+constexpr int GV_ROWS = 64;               // output rows per chunk
+constexpr int GV_RPW = GV_ROWS / GV_WARPS;  // trans = 0 rows per warp
 template <class TA, class TV, class TC>
 __global__ void __launch_bounds__(256) k_gemv(const GTask* __restrict__ tasks,
                                               const GItem* __restrict__ items, VBufs vb,
                                               ABufs ab) {
   const GTask t = tasks[blockIdx.x];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __shared__ TC part[GV_WARPS][32];
+  __shared__ TC part[GV_WARPS][GV_ROWS];
   typedef typename Cx<TC>::R R;
-  for (int r0 = 0; r0 < t.m; r0 += 32) {
-    const int mr = min(32, t.m - r0);
-    TC a1 = czero<TC>();            // trans = 1: row r0 + lane
-    TC a0[4];                       // trans = 0: rows r0 + w + 8q, this lane's share of k
+  for (int r0 = 0; r0 < t.m; r0 += GV_ROWS) {
+    const int mr = min(GV_ROWS, t.m - r0);
+    TC a1[2];                       // trans = 1: rows r0 + lane, r0 + 32 + lane
+    TC a0[GV_RPW];                  // trans = 0: rows r0 + w + 8q, this lane's share of k
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a0[q] = czero<TC>();
+    for (int q = 0; q < 2; ++q) a1[q] = czero<TC>();
+#pragma unroll
+    for (int q = 0; q < GV_RPW; ++q) a0[q] = czero<TC>();
+    GItem In;
+    if (t.it0 < t.it1) In = items[t.it0];
     for (int it = t.it0; it < t.it1; ++it) {
-      const GItem I = items[it];
+      const GItem I = In;
+      if (it + 1 < t.it1) In = items[it + 1];
       const TA* A = (const TA*)ab.p[I.a_buf] + I.a_off;
       const TV* X = (const TV*)vb.p[I.in_buf] + I.in_row;
       if (I.trans) {
-        if (lane < mr) {
-          const TA* Ai = A + r0 + lane;
-          int k = w;
-          for (; k + (GV_UNROLL - 1) * GV_WARPS < I.k; k += GV_UNROLL * GV_WARPS) {
-            TA av[GV_UNROLL];
-            TV xv[GV_UNROLL];
+        const bool v0 = lane < mr, v1 = lane + 32 < mr;
+        const TA* Ai = A + r0 + lane;
+        int k = w;
+        for (; k + (GV_UNROLL - 1) * GV_WARPS < I.k; k += GV_UNROLL * GV_WARPS) {
+          TA av0[GV_UNROLL], av1[GV_UNROLL];
+          TV xv[GV_UNROLL];
 #pragma unroll
-            for (int u = 0; u < GV_UNROLL; ++u) {
-              av[u] = Ai[(long long)(k + u * GV_WARPS) * I.lda];
-              xv[u] = X[k + u * GV_WARPS];
-            }
-#pragma unroll
-            for (int u = 0; u < GV_UNROLL; ++u) cmac(a1, cvt<TC, TA>(av[u]), cvt<TC, TV>(xv[u]));
+          for (int u = 0; u < GV_UNROLL; ++u) {
+            const long long o = (long long)(k + u * GV_WARPS) * I.lda;
+            av0[u] = v0 ? Ai[o] : TA{};
+            av1[u] = v1 ? Ai[o + 32] : TA{};
+            xv[u] = X[k + u * GV_WARPS];
           }
-          for (; k < I.k; k += GV_WARPS)
-            cmac(a1, cvt<TC, TA>(Ai[(long long)k * I.lda]), cvt<TC, TV>(X[k]));
+#pragma unroll
+          for (int u = 0; u < GV_UNROLL; ++u) {
+            cmac(a1[0], cvt<TC, TA>(av0[u]), cvt<TC, TV>(xv[u]));
+            cmac(a1[1], cvt<TC, TA>(av1[u]), cvt<TC, TV>(xv[u]));
+          }
+        }
+        for (; k < I.k; k += GV_WARPS) {
+          const long long o = (long long)k * I.lda;
+          const TC xk = cvt<TC, TV>(X[k]);
+          if (v0) cmac(a1[0], cvt<TC, TA>(Ai[o]), xk);
+          if (v1) cmac(a1[1], cvt<TC, TA>(Ai[o + 32]), xk);
         }
       } else {
-        // the warp's four rows, their loads issued together
+        // the warp's rows, their loads issued together
         for (int k0 = 0; k0 < I.k; k0 += 32) {
           const int k = k0 + lane;
-          TA av[4];
+          TA av[GV_RPW];
           TV xv = k < I.k ? X[k] : TV{};
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < GV_RPW; ++q) {
             const int i = w + 8 * q;
             av[q] = (i < mr && k < I.k) ? A[(long long)(r0 + i) * I.lda + k] : TA{};
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) cmac(a0[q], cvt<TC, TA>(av[q]), cvt<TC, TV>(xv));
+          for (int q = 0; q < GV_RPW; ++q) cmac(a0[q], cvt<TC, TA>(av[q]), cvt<TC, TV>(xv));
         }
       }
     }
     // shuffle-reduce the trans = 0 partials of the warp's rows
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < GV_RPW; ++q) {
       R re = a0[q].x, im = a0[q].y;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -240,28 +257,33 @@ __global__ void __launch_bounds__(256) k_gemv(const GTask* __restrict__ tasks,
       a0[q].x = re;
       a0[q].y = im;
     }
-    TC mine = a1;                    // this warp's partial of row r0 + lane
+    // this warp's partials of rows r0 + lane and r0 + 32 + lane
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (lane == w + 8 * q) {
-        mine.x += a0[q].x;
-        mine.y += a0[q].y;
-      }
-    part[w][lane] = mine;
+    for (int h = 0; h < 2; ++h) {
+      TC mine = a1[h];
+#pragma unroll
+      for (int q = 0; q < GV_RPW; ++q)
+        if (lane + 32 * h == w + 8 * q) {
+          mine.x += a0[q].x;
+          mine.y += a0[q].y;
+        }
+      part[w][lane + 32 * h] = mine;
+    }
     __syncthreads();
-    if (w == 0 && lane < mr) {
-      TC v = part[0][lane];
+    if (threadIdx.x < mr) {
+      const int i = threadIdx.x;
+      TC v = part[0][i];
 #pragma unroll
       for (int q = 1; q < GV_WARPS; ++q) {
-        v.x += part[q][lane].x;
-        v.y += part[q][lane].y;
+        v.x += part[q][i].x;
+        v.y += part[q][i].y;
       }
       if (t.mode == 1) {
-        const TC b = cvt<TC, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + r0 + lane]);
+        const TC b = cvt<TC, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + r0 + i]);
         v.x += b.x;
         v.y += b.y;
       }
-      ((TV*)vb.p[t.out_buf])[t.out_row + r0 + lane] = cvt<TV, TC>(v);
+      ((TV*)vb.p[t.out_buf])[t.out_row + r0 + i] = cvt<TV, TC>(v);
     }
     __syncthreads();
   }
@@ -702,17 +724,21 @@ int grid_for(long long n) {
 
 }  // namespace
 
-// the bulk-copy kernel takes the list: tasks of at most 256 rows, every stored
-// row of an item at most GB_CHUNK bytes, no stacked tasks
+// The bulk-copy kernel takes a list whose items are all transposed blocks
+// stored as whole contiguous rows (lda equal to the task's rows): every piece
+// is then one copy of whole stored rows, and each thread walks its own row
+// through shared memory.  Tasks of at most 256 rows, stored rows of at most
+// GB_CHUNK bytes, no stacked tasks.  (Measured on the 2-lambda sphere: 1.2 to
+// 1.6 TB/s on such launches, against 0.5 to 0.9 TB/s for k_gemv; lists with
+// untransposed blocks ran faster on k_gemv, whose lanes read along the rows.)
 static bool bulk_ok_for(const TaskList& tl) {
   if (tl.bulk_ok < 0) {
-    bool ok = true;
+    bool ok = !tl.tasks.empty();
     for (const GTask& t : tl.tasks) {
-      if (t.mode == 2 || t.m > 256) { ok = false; break; }
+      if (t.mode == 2 || t.m > 256 || t.m <= 0) { ok = false; break; }
       for (int q = t.it0; q < t.it1 && ok; ++q) {
         const GItem& I = tl.items[q];
-        const int len = I.trans ? t.m : I.k;
-        if (len * 16 > GB_CHUNK || len <= 0 || I.lda < len) ok = false;
+        if (!I.trans || I.lda != t.m || t.m * 16 > GB_CHUNK) ok = false;
       }
       if (!ok) break;
     }
