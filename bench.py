@@ -83,8 +83,9 @@ def parse():
     ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
     ap.add_argument("--chunk", type=int, default=120,
                     help="RHS per call of --workload sphere_r10_L7")
-    ap.add_argument("--fill", default="B", choices=["A", "B"],
-                    help="scaling reading of --workload sphere_r10_L7")
+    ap.add_argument("--fill", default=None, choices=["A", "B"],
+                    help="scaling reading: A (full fill; default) or B (near-pattern fill; "
+                         "the default of --workload sphere_r10_L7)")
     ap.add_argument("--oracle-check", action="store_true",
                     help="sphere_r10_L7: oracle series on the library's blocks (8 RHS)")
     ap.add_argument("--levels", type=int, nargs="+", default=[3, 4, 5, 6],
@@ -918,6 +919,7 @@ def run_scaling(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sol = hp.Solver.build(v, f, leaf_max=128, aca_tol=1e-4, ordering=hp.HM_ORDER_ND,
+                                  fill=hp.HM_FILL_NEAR if args.fill == "B" else hp.HM_FILL_FULL,
                                   precision=prec, refine_steps=1 if prec == hp.HM_MIXED else 0)
             t_build = time.perf_counter() - t0
             t0 = time.perf_counter()
@@ -944,8 +946,8 @@ def run_scaling(args):
             "n_gpus": ws, "steps": args.steps, "warmup": 1, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "mixed and c128", "data": "synthetic",
             "config": {"workload": "icospheres L" + ",".join(str(L) for L in args.levels) +
-                       ", radius 0.5*2^(L-3) lambda, leaves<=128, ACA 1e-4, ND order, "
-                       "reading A, 362 monostatic RHS and one RHS",
+                       ", radius 0.5*2^(L-3) lambda, leaves<=128, ACA 1e-4, ND order, reading "
+                       + ("B" if args.fill == "B" else "A") + ", 362 monostatic RHS and one RHS",
                        "value_is": "mixed RHS/s at the largest level"},
             "levels": rows}
     if rank == 0:
@@ -1009,7 +1011,7 @@ def run_large(args):
     stream = torch.cuda.current_stream()
     w = get_workload(args.workload)
     v, f = w.build_mesh()
-    fill = hp.HM_FILL_NEAR if args.fill == "B" else hp.HM_FILL_FULL
+    fill = hp.HM_FILL_FULL if args.fill == "A" else hp.HM_FILL_NEAR
     t0 = time.perf_counter()
     sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max, aca_tol=w.aca_tol,
                           ordering=hp.HM_ORDER_ND, fill=fill, precision=hp.HM_MIXED,

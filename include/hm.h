@@ -78,12 +78,19 @@ typedef struct {
                             terms no longer shrink: the ratio of Eq. 45 is at
                             least one), and at n_terms terms in any case.  The
                             solve then synchronises its stream once per term.  */
-  int reserved[4];
+  int autotune;          /* HM_MIXED with tensor cores: 1 (default) times the
+                            candidate split-K sizes of every sweep phase on the
+                            first solve with a new number of 128-RHS tiles and
+                            keeps the fastest (cached per phase shape for the
+                            process); that solve synchronises its stream, so
+                            make it before any stream capture.  0 keeps the
+                            built-in choice                                     */
+  int reserved[3];
 } hm_params;
 
 /* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,
  * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26, tensor_cores 1,
- * fp64_emulation 1, term_tol 0 (fixed term count). */
+ * fp64_emulation 1, term_tol 0 (fixed term count), autotune 1. */
 void hm_default_params(hm_params* p);
 
 /* Build the H-matrix of a closed or open triangulated PEC surface (Sec. II:
@@ -184,8 +191,9 @@ hm_status hm_get_diagnostics(hm_handle h, double* ratio_host, double* resid_host
  * (upper), far factor entries, max rank, forward levels, backward levels,
  * device bytes held, the number of kernels the library has launched in
  * this process so far (all handles; read it before and after a region to
- * count that region's launches), and the number of series terms of the last
- * solve (the largest over its series when refinement steps ran). */
+ * count that region's launches), the number of series terms of the last
+ * solve (the largest over its series when refinement steps ran), and the
+ * number of sweep phases whose split-K size the autotuner has set. */
 hm_status hm_get_stats(hm_handle h, long long* out_host, int n);
 
 /* Copy the leaf-order permutation (N int64, leaf position -> original index)

@@ -27,7 +27,7 @@ HM_FILL_FULL, HM_FILL_NEAR = 0, 1
 OPS = {"RT": 0, "R": 1, "DINV": 2, "FAR": 3, "NEAR": 4, "Z": 5}
 STATS = ("N", "leaves", "near_blocks", "far_blocks", "alpha_entries", "d_entries",
          "near_entries", "far_entries", "max_rank", "fwd_levels", "bwd_levels", "device_bytes",
-         "kernel_launches", "terms_used")
+         "kernel_launches", "terms_used", "tuned_phases")
 
 # every symbol include/hm.h declares
 SYMBOLS = ("hm_default_params", "hm_build", "hm_import", "hm_save", "hm_compute_scaling",
@@ -46,7 +46,7 @@ class hm_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("tensor_cores", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("term_tol", ctypes.c_double),
-                ("reserved", ctypes.c_int * 4)]
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double

@@ -7,7 +7,9 @@
 //   b_o = Z~_N^{-1} b~ (Eq. 32), it_1 = Z~_N^{-1} R^T Z_F R b_o (Eq. 31)
 //   x = R (it_0 - it_1 + ...)  (Eq. 26, 36)
 #include <algorithm>
+#include <array>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -382,6 +384,24 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
       for (const Tgt& tg : tgts) add_target(h, tl, fl, scr_row, tg.out_row, tg.mt, tg.its, kmax);
       max_scr = std::max(max_scr, scr_row);
       if (tl.tasks.empty()) continue;
+      if (kmax != KMAX) {
+        // the partial panels of the smallest split size (the autotuner's
+        // candidates all fit the scratch panel)
+        TaskList t2;
+        FinList f2;
+        int r2 = 0;
+        for (const Tgt& tg : tgts) add_target(h, t2, f2, r2, tg.out_row, tg.mt, tg.its, KMAX);
+        max_scr = std::max(max_scr, r2);
+      }
+      PhaseTargets pt;
+      for (const Tgt& tg : tgts) {
+        if (tg.its.empty()) continue;
+        pt.out_row.push_back(tg.out_row);
+        pt.mt.push_back(tg.mt);
+        pt.its.push_back(tg.its);
+      }
+      pt.kmax = kmax;
+      sw.tgt.push_back(std::move(pt));
       sw.part.push_back(std::move(tl));
       sw.fin.push_back(std::move(fl));
     }
@@ -829,6 +849,195 @@ static hm_status far_stage_split(hm_ctx* h, TaskList& tl, void* in, void* out, i
   return s;
 }
 
+// ------------------------------------------------------------ split-K autotuner
+// For every supernode sweep phase of a mixed-precision handle on the tensor
+// cores: rebuild the phase's lists for the candidate split sizes 128 ... 4096
+// rows (each distinct decomposition once), time the phase (gather and
+// finalize, best of three) on the handle's own buffers and keep the fastest.
+// A choice is cached for the process under the phase's shape -- direction,
+// kind (external gather or T_G product), and the powers of two of its target
+// count, inner rows and widest target, and the 128-RHS tiles -- so handles
+// with phases of the same shape (the scatterers of a batch) take it without
+// timing.  It runs before the solve's data flow: its launches read and write
+// a work panel that every solve fills first.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, long long> g_tune;
+
+int lg2(long long v) {
+  int r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+std::array<int, 6> phase_key(int dir, const PhaseTargets& pt, int ytiles) {
+  long long kin = 0;
+  int mmax = 0;
+  bool tg = false;
+  for (size_t q = 0; q < pt.its.size(); ++q) {
+    mmax = std::max(mmax, pt.mt[q]);
+    for (const GItem& it : pt.its[q]) {
+      kin += it.k;
+      tg |= it.a_buf == AB_TINV;
+    }
+  }
+  return {dir, tg ? 1 : 0, lg2((long long)pt.its.size()), lg2(kin), lg2(mmax), ytiles};
+}
+
+void free_fin(FinList& fl) {
+  cudaFree(fl.d_tasks);
+  cudaFree(fl.d_slots);
+  fl.d_tasks = nullptr;
+  fl.d_slots = nullptr;
+}
+
+// the phase's lists for split size kmax on the device, with their tensor-core tiles
+hm_status make_phase(hm_ctx* h, const PhaseTargets& pt, long long kmax, const ABufs& a,
+                     TaskList& tl, FinList& fl, int& scr) {
+  tl = TaskList();
+  fl = FinList();
+  scr = 0;
+  for (size_t q = 0; q < pt.its.size(); ++q)
+    add_target(h, tl, fl, scr, pt.out_row[q], pt.mt[q], pt.its[q], kmax);
+  split_wide_tasks(tl, 128);
+  hm_status s = upload_tasks(tl, nullptr);
+  if (!s) s = upload_fin(fl, nullptr);
+  if (!s) s = build_tc_tiles(tl, a, nullptr);
+  return s;
+}
+
+// best of three device times of one phase (gather, then finalize)
+hm_status time_phase(hm_ctx* h, const TaskList& tl, const FinList& fl, const VBufs& v,
+                     const ABufs& a, int nrhs, const XSplit& xs, unsigned char* xs0,
+                     float* best) {
+  cudaEvent_t e0, e1;
+  HM_CUDA(cudaEventCreate(&e0));
+  HM_CUDA(cudaEventCreate(&e1));
+  hm_status s = HM_OK;
+  *best = 1e30f;
+  for (int rep = 0; rep < 3 && !s; ++rep) {
+    cudaEventRecord(e0, h->stream);
+    s = launch_tasks_tc(tl, v, a, nrhs, h->stream, h->p.spin_limit, h->d_err, &xs);
+    if (!s) s = launch_fin_split(fl, v, nrhs, xs0, xs.J[0], xs.G, h->stream);
+    cudaEventRecord(e1, h->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess && !s) s = cuda_status(e);
+    *best = std::min(*best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  // a bounded wait that ran out makes the timing meaningless: the caller stops
+  // tuning (the error word stays set for hm_get_diagnostics)
+  int e = 0;
+  HM_CUDA(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return e ? HM_ERR_TIMEOUT : HM_OK;
+}
+}  // namespace
+
+hm_status tune_sweeps(hm_ctx* h, int nrhs) {
+  if (h->p.precision != HM_MIXED || !h->p.tensor_cores || !h->p.autotune || nrhs < 32)
+    return HM_OK;
+  const int yt = (nrhs + 127) / 128;
+  if (h->fwd.tuned_ytiles == yt && h->bwd.tuned_ytiles == yt) return HM_OK;
+  XSplit xs;
+  unsigned char* bufs[2];
+  if (!mixed_xsplit(h, &xs, bufs)) return HM_OK;
+  hm_status s = ensure_err(h);
+  if (s) return s;
+  // a work panel of N x nrhs complex64 values (the complex128 panel P_Y, not
+  // in use before the solve's residual) and its split panel
+  void* buf = h->d_vec[P_Y];
+  VBufs v;
+  ABufs a;
+  tables(h, buf, buf, true, v, a);
+  s = launch_split((const float2*)buf, h->N, nrhs, bufs[0], xs.J[0], xs.G, h->stream);
+  if (s) return s;
+  const int scr_cap = std::max(h->fwd.scratch_rows, h->bwd.scratch_rows);
+  int dir = 0;
+  for (Sweep* sw : {&h->fwd, &h->bwd}) {
+    if (sw->tuned_ytiles == yt || sw->tgt.size() != sw->part.size()) {
+      ++dir;
+      continue;
+    }
+    for (size_t l = 0; l < sw->part.size(); ++l) {
+      PhaseTargets& pt = sw->tgt[l];
+      if (!tc_ok_for(sw->part[l]) || !sw->part[l].d_tiles) continue;
+      const auto key = phase_key(dir, pt, yt);
+      long long want = -1;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) want = it->second;
+      }
+      if (want < 0) {
+        float best_ms = 0.f;
+        s = time_phase(h, sw->part[l], sw->fin[l], v, a, nrhs, xs, bufs[0], &best_ms);
+        if (s == HM_ERR_TIMEOUT) return HM_OK;   // keep the built-in choices
+        if (s) return s;
+        long long best_k = pt.kmax;
+        std::vector<std::pair<size_t, size_t>> seen{{sw->part[l].tasks.size(),
+                                                     sw->fin[l].slots.size()}};
+        for (long long km = 128; km <= 4096; km *= 2) {
+          if (km == pt.kmax) continue;
+          TaskList tl;
+          FinList fl;
+          int scr = 0;
+          s = make_phase(h, pt, km, a, tl, fl, scr);
+          const std::pair<size_t, size_t> cnt{tl.tasks.size(), fl.slots.size()};
+          const bool dup = std::find(seen.begin(), seen.end(), cnt) != seen.end();
+          float ms = 1e30f;
+          if (!s && !dup && scr <= scr_cap && tl.d_tiles) {
+            seen.push_back(cnt);
+            s = time_phase(h, tl, fl, v, a, nrhs, xs, bufs[0], &ms);
+          }
+          free_tasks(tl);
+          free_fin(fl);
+          if (s == HM_ERR_TIMEOUT) return HM_OK;
+          if (s) return s;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_k = km;
+          }
+        }
+        want = best_k;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = want;
+      }
+      if (want != pt.kmax) {
+        TaskList tl;
+        FinList fl;
+        int scr = 0;
+        s = make_phase(h, pt, want, a, tl, fl, scr);
+        if (s || scr > scr_cap || !tl.d_tiles) {
+          free_tasks(tl);
+          free_fin(fl);
+          if (s) return s;
+          continue;
+        }
+        h->dev_bytes += tl.tile_bytes;
+        h->dev_bytes -= std::min(h->dev_bytes, sw->part[l].tile_bytes);
+        free_tasks(sw->part[l]);
+        free_fin(sw->fin[l]);
+        sw->part[l] = tl;
+        sw->fin[l] = fl;
+        pt.kmax = want;
+        ++h->gen;              // a graph recorded before refers to the old lists
+      }
+      ++h->tuned_phases;
+    }
+    sw->tuned_ytiles = yt;
+    ++dir;
+  }
+  HM_CUDA(cudaStreamSynchronize(h->stream));
+  return HM_OK;
+}
+
 hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs) {
   XSplit xs;
   unsigned char* bufs[2];
@@ -978,6 +1187,7 @@ void hm_default_params(hm_params* p) {
   p->spin_limit = 1LL << 26;
   p->tensor_cores = 1;
   p->fp64_emulation = 1;
+  p->autotune = 1;
 }
 
 const char* hm_status_string(hm_status s) {
@@ -1422,11 +1632,11 @@ hm_status hm_get_stats(hm_handle h, long long* out, int n) {
   for (int k = 0; k < (int)h->rows.size(); ++k)
     for (int j : h->rows[k]) a_e += (long long)h->m[h->elim[k]] * h->m[h->elim[j]];
   for (int k = 0; k < h->nl; ++k) d_e += (long long)h->m[k] * h->m[k];
-  long long v[14] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
+  long long v[15] = {h->N, h->nl, (long long)h->near.size(), (long long)h->far.size(), a_e, d_e,
                      near_e, far_e, maxr, (long long)h->fwd.part.size(),
                      (long long)h->bwd.part.size(), (long long)h->dev_bytes, hm::launch_count(),
-                     h->last_terms};
-  for (int i = 0; i < n && i < 14; ++i) out[i] = v[i];
+                     h->last_terms, h->tuned_phases};
+  for (int i = 0; i < n && i < 15; ++i) out[i] = v[i];
   return HM_OK;
 }
 

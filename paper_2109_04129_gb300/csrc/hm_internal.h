@@ -93,10 +93,19 @@ struct FinList {
   int* d_slots = nullptr;
 };
 // One sweep = a sequence of levels, each a partial launch and a finalize.
+// The targets of one sweep phase (output rows, rows, items), kept so that the
+// split-K autotuner can rebuild the phase's lists with another split size.
+struct PhaseTargets {
+  std::vector<int> out_row, mt;
+  std::vector<std::vector<GItem>> its;
+  long long kmax = 0;     // split size of the lists in use
+};
 struct Sweep {
   std::vector<TaskList> part;
   std::vector<FinList> fin;
+  std::vector<PhaseTargets> tgt;   // per part (supernode sweeps only)
   int scratch_rows = 0;   // rows of VB_SCR needed
+  int tuned_ytiles = 0;   // RHS tiles the split sizes were tuned for (0: not tuned)
 };
 
 enum { PC_FWD = 0, PC_BWD = 1, PC_FIN = 2, PC_DINV = 3, PC_FAR1 = 4, PC_FAR2 = 5,
@@ -182,6 +191,7 @@ struct hm_ctx {
   size_t evused = 0;
   std::vector<double> ratio, resid;
   int last_terms = 0;           // series terms of the last solve (largest over its series)
+  int tuned_phases = 0;         // sweep phases whose split size the autotuner set
   size_t dev_bytes = 0;
   // bumped whenever device buffers or task lists are replaced; a grouped-solve
   // graph captured under another value refers to freed memory and is rebuilt

@@ -22,6 +22,7 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
 hm_status mixed_far(hm_ctx* h, void* in, void* out, int nrhs);
 hm_status run_oz_list(hm_ctx* h, TaskList& tl, RowExp& R, void* in, void* out, int nrhs,
                       int cat, bool panels32 = false);
+hm_status tune_sweeps(hm_ctx* h, int nrhs);
 }
 
 namespace {
@@ -238,6 +239,8 @@ hm_status hm_mixed_solve(hm_ctx* h, cplx* X, const cplx* B, int nrhs) {
   if (!M || !h->has_scaling) return HM_ERR_STATE;
   hm_status s = ensure32(h, M, nrhs);
   if (s) return s;
+  // split sizes of the tensor-core sweeps, timed once per number of RHS tiles
+  if ((s = tune_sweeps(h, nrhs))) return s;
   cplx** V = h->d_vec;
   const size_t n = (size_t)h->N * nrhs;
   // b in leaf order: FP64 (for the residual) and FP32 (for the series)
