@@ -655,6 +655,8 @@ hm_status ensure_buffers(hm_ctx* h, int nrhs) {
   // series panels (and the FP64 refinement copies) are not needed there
   if (h->p.precision == HM_MIXED)
     for (int i : {(int)P_BO, (int)P_IT, (int)P_SCR, (int)P_X0, (int)P_B0}) rows[i] = 1;
+  // the staging panels of host-buffer solves are sized by the first such solve
+  rows[P_HB] = rows[P_HX] = 1;
   for (int i = 0; i < NPHYS; ++i) {
     HM_CUDA(cudaMalloc((void**)&h->d_vec[i], rows[i] * nrhs * sizeof(cplx)));
     h->vec_rows[i] = rows[i];
@@ -755,6 +757,10 @@ static hm_status launch_any(hm_ctx* h, const TaskList& tl, const VBufs& v, const
 
 hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs, int cat,
                          int prec, bool low) {
+  if (low && prec == PREC_32) {       // complex64 matrices on the CUDA cores
+    hm_status s = mixed_ensure_c64(h);
+    if (s) return s;
+  }
   VBufs v;
   ABufs a;
   tables(h, in, out, low, v, a);
@@ -767,9 +773,6 @@ hm_status run_chain_list(hm_ctx* h, TaskList& tl, void* in, void* out, int nrhs,
 
 hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, int prec,
                           bool low) {
-  VBufs v;
-  ABufs a;
-  tables(h, buf, buf, low, v, a);
   double asz = prec == PREC_32 ? 8 : 16, vsz = prec == PREC_64 ? 16 : 8;
   // complex64 sweeps on the tensor cores read the sweep buffer through its
   // split panel: split once here, then every finalize keeps it current
@@ -778,6 +781,15 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
   const bool split = prec == PREC_32 && low && h->p.tensor_cores && nrhs >= 32 &&
                      mixed_xsplit(h, &xs, bufs);
   hm_status s;
+  if (low && prec == PREC_32) {
+    // a phase on the CUDA cores reads the complex64 matrices
+    bool simt = !split;
+    for (const TaskList& tl : sw.part) simt |= !tc_ok_for(tl);
+    if (simt && (s = mixed_ensure_c64(h))) return s;
+  }
+  VBufs v;
+  ABufs a;
+  tables(h, buf, buf, low, v, a);
   if (split) {
     s = ensure_err(h);
     if (s) return s;
@@ -949,6 +961,7 @@ hm_status tune_sweeps(hm_ctx* h, int nrhs) {
   unsigned char* bufs[2];
   if (!mixed_xsplit(h, &xs, bufs)) return HM_OK;
   hm_status s = ensure_err(h);
+  if (!s) s = mixed_ensure_c64(h);       // the candidates' tiles are cut from them
   if (s) return s;
   // a work panel of N x nrhs complex64 values (the complex128 panel P_Y, not
   // in use before the solve's residual) and its split panel
@@ -1035,6 +1048,7 @@ hm_status tune_sweeps(hm_ctx* h, int nrhs) {
     ++dir;
   }
   HM_CUDA(cudaStreamSynchronize(h->stream));
+  mixed_drop_c64(h);                     // every tensor-core list has its tiles
   return HM_OK;
 }
 
@@ -1581,6 +1595,14 @@ hm_status hm_power_series_solve_host(hm_handle h, void* X_host, const void* B_ho
   if (!X_host || !B_host || nrhs <= 0) return HM_ERR_INVALID;
   try {
     if ((s = ensure_buffers(h, nrhs))) return s;
+    for (int i : {(int)P_HB, (int)P_HX})
+      if (h->vec_rows[i] != (size_t)h->N) {
+        cudaFree(h->d_vec[i]);
+        h->d_vec[i] = nullptr;
+        h->vec_rows[i] = 0;
+        HM_CUDA(cudaMalloc((void**)&h->d_vec[i], (size_t)h->N * h->cap_nrhs * sizeof(cplx)));
+        h->vec_rows[i] = (size_t)h->N;
+      }
     size_t bytes = (size_t)h->N * nrhs * sizeof(cplx);
     cplx* dB = h->d_vec[P_HB];
     cplx* dX = h->d_vec[P_HX];

@@ -35,6 +35,11 @@ struct Mixed {
   float2* tinv = nullptr;
   float2* v[NQ] = {nullptr};
   int cap = 0;
+  // the complex64 matrix copies are freed once every tensor-core list has its
+  // bf16 tiles (the tensor-core kernels read only the tiles); a CUDA-core
+  // launch (fewer than 32 RHS) or a new tiling rebuilds them from the host
+  // copies first
+  bool dropped = false;
 };
 
 template <class T>
@@ -143,6 +148,7 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   if (s) return s;
   if (h->has_scaling) s = to32(h->h_alpha, &M->alpha);
   if (!s && h->has_scaling) s = to32(h->h_tinv, &M->tinv);
+  M->dropped = false;
   if (!s && h->has_scaling) {
     // a mixed-precision handle never runs the FP64 sweeps: their complex128
     // coefficients stay on the host only (hm_save writes the host copies)
@@ -166,7 +172,11 @@ hm_status hm_mixed_prepare(hm_ctx* h) {
   // the far-field inputs are fixed during a launch: they arrive as split
   // panels, and the tiles of the far lists are built for that
   if ((s = build_tc_tiles(h->far1s_tl, a, &h->dev_bytes))) return s;
-  return build_tc_tiles(h->far2_tl, a, &h->dev_bytes);
+  if ((s = build_tc_tiles(h->far2_tl, a, &h->dev_bytes))) return s;
+  // with the autotuner on, the copies stay until the first tuning (it builds
+  // tiles of its own from them)
+  if (!h->p.autotune) mixed_drop_c64(h);
+  return HM_OK;
 }
 
 void hm_mixed_release(hm_ctx* h) {
@@ -181,6 +191,26 @@ void hm_mixed_release(hm_ctx* h) {
 }
 
 namespace hm {
+hm_status mixed_ensure_c64(hm_ctx* h) {
+  Mixed* M = (Mixed*)h->mixed;
+  if (!M || !M->dropped) return HM_OK;
+  hm_status s = to32(h->h_far, &M->far);
+  if (!s && h->has_scaling) s = to32(h->h_alpha, &M->alpha);
+  if (!s && h->has_scaling) s = to32(h->h_tinv, &M->tinv);
+  if (s) return s;
+  M->dropped = false;
+  ++h->gen;                 // a graph recorded before refers to other buffers
+  return HM_OK;
+}
+void mixed_drop_c64(hm_ctx* h) {
+  Mixed* M = (Mixed*)h->mixed;
+  if (!M || M->dropped || !h->p.tensor_cores) return;
+  dfree(M->far);
+  dfree(M->alpha);
+  dfree(M->tinv);
+  M->dropped = true;
+  ++h->gen;
+}
 const void* mixed_alpha(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->alpha : nullptr; }
 const void* mixed_far_data(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->far : nullptr; }
 const void* mixed_tinv(hm_ctx* h) { return h->mixed ? ((Mixed*)h->mixed)->tinv : nullptr; }

@@ -540,47 +540,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
         ++g;
         return true;
       };
-      // The matrix values of a stage are loaded two stages ahead of its
-      // slicing: the global-memory latency of the loads overlaps the slicing
-      // and storing of the two stages before (the MMA thread needs a stage's
-      // digits sooner than one load latency after the previous stage's).
-      const int iend = task_it_end(t);
-      int itA = t.it0, stA = 0;
-      while (itA < iend && oz_nst(items[itA]) == 0) ++itA;
-      int itB = iend, stB = 0, itC = iend, stC = 0;
-      double2 avA[EQ], avB[EQ], avC[EQ];
-      int exA[EQ], exB[EQ], exC[EQ];
-      if (itA < iend) {
-        load(itA, stA, avA, exA);
-        next(itA, stA, itB, stB);
-      }
-      if (itB < iend) {
-        load(itB, stB, avB, exB);
-        next(itB, stB, itC, stC);
-      }
-      while (itA < iend && !stop) {
-        if (itC < iend) load(itC, stC, avC, exC);
-        if (!put(itA, avA, exA)) {
+      // loads of a stage are issued before the wait for its buffer
+      int it = t.it0, st = 0;
+      while (it < task_it_end(t) && oz_nst(items[it]) == 0) ++it;
+      double2 av[EQ];
+      int ex[EQ];
+      while (it < task_it_end(t) && !stop) {
+        load(it, st, av, ex);
+        if (!put(it, av, ex)) {
           stop = true;
           break;
         }
-        itA = itB;
-        stA = stB;
-        itB = itC;
-        stB = stC;
-#pragma unroll
-        for (int q = 0; q < EQ; ++q) {
-          avA[q] = avB[q];
-          exA[q] = exB[q];
-          avB[q] = avC[q];
-          exB[q] = exC[q];
-        }
-        if (itC < iend) {
-          int it2, st2;
-          next(itC, stC, it2, st2);
-          itC = it2;
-          stC = st2;
-        }
+        int it2, st2;
+        next(it, st, it2, st2);
+        it = it2;
+        st = st2;
       }
     }
   } else {
