@@ -130,37 +130,6 @@ void free_sweep(Sweep& sw) {
   sw.fin.clear();
 }
 
-// Targets of a sweep phase that no task of the same phase reads (external
-// gathers, leaf-level sweeps) and that have a single split-K task: the task
-// writes out = base + acc in place and, on the tensor cores, the split panel
-// too (mode 3), and the target leaves the finalize list.  The sum is the same
-// one addition the finalize would make (base + the only partial).
-void finish_single_targets(TaskList& tl, FinList& fl) {
-  FinList nf;
-  for (const FTask& f : fl.tasks) {
-    if (f.s1 - f.s0 != 1) {
-      FTask g = f;
-      g.s0 = (int)nf.slots.size();
-      for (int q = f.s0; q < f.s1; ++q) nf.slots.push_back(fl.slots[q]);
-      g.s1 = (int)nf.slots.size();
-      nf.tasks.push_back(g);
-      continue;
-    }
-    const int slot = fl.slots[f.s0];
-    for (GTask& t : tl.tasks) {
-      if (t.out_buf != VB_SCR || t.out_row < slot || t.out_row >= slot + f.m) continue;
-      const int dr = t.out_row - slot;
-      t.mode = 3;
-      t.out_buf = f.out_buf;
-      t.out_row = f.out_row + dr;
-      t.base_buf = f.base_buf;
-      t.base_row = f.base_row + dr;
-    }
-  }
-  fl.tasks.swap(nf.tasks);
-  fl.slots.swap(nf.slots);
-}
-
 // One sweep over the alpha pattern.  forward: b~_j += sum_k alpha_kj^T b~_k
 // (targets j, predecessors k < j); backward: x_k += sum_j alpha_kj x_j
 // (targets k, successors j > k).  Levels: a target waits for all of its
@@ -242,8 +211,6 @@ void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
       fl.tasks.push_back(ft);
     }
     max_scr = std::max(max_scr, scr_row);
-    // every source of a level is final before it: no task reads a target row
-    finish_single_targets(tl, fl);
   }
   sw.scratch_rows = max_scr;
 }
@@ -426,9 +393,6 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
         for (const Tgt& tg : tgts) add_target(h, t2, f2, r2, tg.out_row, tg.mt, tg.its, KMAX);
         max_scr = std::max(max_scr, r2);
       }
-      // phase 0 reads only rows of earlier group levels; phase 1 (T_G) reads
-      // rows of its own group, which its targets overwrite
-      if (phase == 0) finish_single_targets(tl, fl);
       PhaseTargets pt;
       for (const Tgt& tg : tgts) {
         if (tg.its.empty()) continue;
@@ -437,7 +401,6 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
         pt.its.push_back(tg.its);
       }
       pt.kmax = kmax;
-      pt.direct = phase == 0;
       sw.tgt.push_back(std::move(pt));
       sw.part.push_back(std::move(tl));
       sw.fin.push_back(std::move(fl));
@@ -466,7 +429,7 @@ void split_wide_tasks(TaskList& tl, int mmax) {
       if (t.mode != 2) {
         sl.m = std::min(step, t.m - r);
         sl.out_row = t.out_row + r;
-        if (task_has_base(t)) sl.base_row = t.base_row + r;
+        if (t.mode == 1) sl.base_row = t.base_row + r;
       }
       sl.it0 = (int)ni.size();
       for (int q = t.it0; q < t.it1; ++q) {
@@ -844,7 +807,6 @@ hm_status run_chain_sweep(hm_ctx* h, Sweep& sw, void* buf, int nrhs, int cat, in
       s = launch_any(h, tl, v, a, nrhs, prec);
     if (s) return s;
     prof_end(h, ev, cat, tl_bytes(tl, nrhs, asz, vsz), 8.0 * tl.flops * nrhs);
-    if (sw.fin[l].tasks.empty()) continue;     // every target finished by its task
     ev = prof_begin(h);
     s = split ? launch_fin_split(sw.fin[l], v, nrhs, bufs[0], xs.J[0], xs.G, h->stream)
               : launch_fin(sw.fin[l], v, nrhs, h->stream, prec);
@@ -952,7 +914,6 @@ hm_status make_phase(hm_ctx* h, const PhaseTargets& pt, long long kmax, const AB
   scr = 0;
   for (size_t q = 0; q < pt.its.size(); ++q)
     add_target(h, tl, fl, scr, pt.out_row[q], pt.mt[q], pt.its[q], kmax);
-  if (pt.direct) finish_single_targets(tl, fl);
   split_wide_tasks(tl, 128);
   hm_status s = upload_tasks(tl, nullptr);
   if (!s) s = upload_fin(fl, nullptr);

@@ -20,17 +20,10 @@ typedef double2 cplx;   // complex128 as (re, im)
 //   mode 2 (stacked, tensor-core engines only): the items are row segments
 //     of one operator over the same input rows (those of item it0): out rows
 //     [r0, r0 + nrow) = op(A_item) * in
-//   mode 3 (sweep target finished by its only task): out = base + acc as in
-//     mode 1, and the tensor-core engine also writes the three bf16 slices of
-//     the result into the split panel of its input buffer (what the sweep
-//     finalize does for targets of several tasks)
 // Panels live in "vector buffers" with row stride nrhs (RHS fastest).
 struct GTask {
   int out_buf, out_row, m, it0, it1, base_buf, base_row, mode;
 };
-__host__ __device__ inline bool task_has_base(const GTask& t) {
-  return t.mode == 1 || t.mode == 3;
-}
 // op(A) is m x k: trans = 0 -> A[r * lda + c]; trans = 1 -> A[c * lda + r].
 struct GItem {
   long long a_off;
@@ -106,8 +99,6 @@ struct PhaseTargets {
   std::vector<int> out_row, mt;
   std::vector<std::vector<GItem>> its;
   long long kmax = 0;     // split size of the lists in use
-  bool direct = false;    // no task reads rows this phase writes (single-task
-                          // targets may be finished by their task, mode 3)
 };
 struct Sweep {
   std::vector<TaskList> part;

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(NTHR) k_gather_gemm(const GTask* __restrict__ 
       if (klane != 0) continue;
     }
     TV* out = (TV*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
-    const TV* base = task_has_base(t) ? (const TV*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
+    const TV* base = (t.mode == 1) ? (const TV*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
                                    : nullptr;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_gemv(const GTask* __restrict__ tasks,
         v.x += part[q][i].x;
         v.y += part[q][i].y;
       }
-      if (task_has_base(t)) {
+      if (t.mode == 1) {
         const TC b = cvt<TC, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + r0 + i]);
         v.x += b.x;
         v.y += b.y;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(GB_THREADS) k_gemv_bulk(const GTask* __restric
       v.x += p.x;
       v.y += p.y;
     }
-    if (task_has_base(t)) {
+    if (t.mode == 1) {
       const double2 bv = cvt<double2, TV>(((const TV*)vb.p[t.base_buf])[t.base_row + tid]);
       v.x += bv.x;
       v.y += bv.y;
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256) k_gather_rows(const GTask* __restrict__ t
     }
     if (col < nrhs) {
       TV* out = (TV*)vb.p[t.out_buf] + (long long)(t.out_row + r0) * nrhs;
-      const TV* base = task_has_base(t)
+      const TV* base = (t.mode == 1)
                            ? (const TV*)vb.p[t.base_buf] + (long long)(t.base_row + r0) * nrhs
                            : nullptr;
 #pragma unroll

@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gather(
       if (open && !stop) drain(cur);
       if (stop || col >= nrhs) continue;
       TY* out = (TY*)vb.p[t.out_buf] + (long long)(t.out_row + rp) * nrhs;
-      const TY* base = task_has_base(t)
+      const TY* base = (t.mode == 1)
                            ? (const TY*)vb.p[t.base_buf] + (long long)(t.base_row + rp) * nrhs
                            : nullptr;
 #pragma unroll

@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
       for (int it = t.it0; it < task_it_end(t) && !has; ++it) has = tc_nst(items[it]) > 0;
       const int n_real = tc_nreal(t.m);
       float2* out = (float2*)vb.p[t.out_buf] + (long long)t.out_row * nrhs;
-      const float2* base = task_has_base(t) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
+      const float2* base = (t.mode == 1) ? (const float2*)vb.p[t.base_buf] + (long long)t.base_row * nrhs
                                          : nullptr;
       if (!has) {                              // no inner rows: out = base (or 0)
         if (col < nrhs)
@@ -502,20 +502,6 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
                 yv.y += bv.y;
               }
               out[(long long)i * nrhs + col] = yv;
-              if (t.mode == 3) {
-                // the target's only task: its slices go to the split panel of
-                // the sweep buffer here (no task of this launch reads them)
-                const long long row = t.out_row + i;
-                __nv_bfloat16 sr[TC_NS], si[TC_NS];
-                split3(yv.x, sr);
-                split3(yv.y, si);
-                unsigned char* xw = (unsigned char*)xsp.xs[0];
-#pragma unroll
-                for (int q = 0; q < TC_NS; ++q)
-                  *(uint32_t*)(xw + xs_off(q, xsp.G / 16, col >> 7, xsp.J[0], row >> 2,
-                                           (col >> 3) & 15, col & 7) + (row & 3) * 4) =
-                      pack2(sr[q], si[q]);
-              }
             }
           }
         }
