@@ -82,6 +82,11 @@ namespace {
 
 const long long KMAX = 128;   // inner rows per split-K task of a sweep (more CTAs on
                               // the narrow top levels of the elimination tree)
+// largest split size of the tensor-core sweeps: a task's FP32 sums in tensor
+// memory run over at most this many inner rows (longer sums cost accuracy;
+// measured on the 2-lambda sphere: mixed error 6.6-7.5e-5 with splits up to
+// 4096 rows against the 1e-4 bar)
+const long long KMAX_TC = 2048;
 
 template <class T>
 hm_status upload(T** dptr, const std::vector<T>& v, size_t* bytes) {
@@ -355,8 +360,8 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
       // Split-K size of the phase.  The FP64 gather kernels want many small
       // tasks (KMAX); the persistent tensor-core kernel needs only enough tasks
       // to keep its CTAs busy, and every extra split is one more partial panel
-      // for the finalize to read: take the largest size that keeps
-      // min(TC_TASK_GOAL, tasks at KMAX) tasks.
+      // for the finalize to read: take the largest size (up to KMAX_TC) that
+      // keeps min(TC_TASK_GOAL, tasks at KMAX) tasks.
       long long kmax = KMAX;
       if (h->p.precision == HM_MIXED && h->p.tensor_cores) {
         auto count = [&](long long km) {
@@ -375,7 +380,7 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
         };
         constexpr long long TC_TASK_GOAL = 300;
         const long long goal = std::min(TC_TASK_GOAL, count(KMAX));
-        for (long long km = 4096; km > KMAX; km /= 2)
+        for (long long km = KMAX_TC; km > KMAX; km /= 2)
           if (count(km) >= goal) {
             kmax = km;
             break;
@@ -863,7 +868,7 @@ static hm_status far_stage_split(hm_ctx* h, TaskList& tl, void* in, void* out, i
 
 // ------------------------------------------------------------ split-K autotuner
 // For every supernode sweep phase of a mixed-precision handle on the tensor
-// cores: rebuild the phase's lists for the candidate split sizes 128 ... 4096
+// cores: rebuild the phase's lists for the candidate split sizes 128 ... 2048
 // rows (each distinct decomposition once), time the phase (gather and
 // finalize, best of three) on the handle's own buffers and keep the fastest.
 // A choice is cached for the process under the phase's shape -- direction,
@@ -996,7 +1001,7 @@ hm_status tune_sweeps(hm_ctx* h, int nrhs) {
         long long best_k = pt.kmax;
         std::vector<std::pair<size_t, size_t>> seen{{sw->part[l].tasks.size(),
                                                      sw->fin[l].slots.size()}};
-        for (long long km = 128; km <= 4096; km *= 2) {
+        for (long long km = KMAX; km <= KMAX_TC; km *= 2) {
           if (km == pt.kmax) continue;
           TaskList tl;
           FinList fl;

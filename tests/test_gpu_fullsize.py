@@ -81,7 +81,7 @@ def test_full_size_benchmarked_schedule(full_case):
     alpha, D^-1 and T_G itself (hm_compute_scaling on the GPU, from the
     oracle's H-matrix and leaf centres); then the FP64 chain and the mixed
     chain (tcgen05 sweeps over the supernodes, tcgen05 far field, FP64-accurate
-    residual, split-K up to 4096 rows) solve every RHS, compared with the
+    residual, split-K up to 2048 rows) solve every RHS, compared with the
     oracle's series and series + refinement on the same H in the same order."""
     import torch
     import paper_2109_04129_gb300 as hp
