@@ -80,6 +80,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single-rhs", action="store_true",
                     help="skip the one-RHS (bandwidth-bound) leg")
+    ap.add_argument("--split-max", type=int, default=0,
+                    help="largest split-K size of the tensor-core sweeps (0: the library's)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-tensor-cores", action="store_true",
+                    help="the mixed chain on the CUDA cores (FP32 arithmetic), for comparison")
     ap.add_argument("--cpu-rhs", type=int, default=4, help="RHS in the oracle's timed sample")
     ap.add_argument("--chunk", type=int, default=120,
                     help="RHS per call of --workload sphere_r10_L7")
@@ -477,7 +482,8 @@ def run_native(args):
     sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max,
                           aca_tol=w.aca_tol,
                           ordering=hp.HM_ORDER_ND if args.ordering == "nd" else hp.HM_ORDER_DFS,
-                          precision=prec, refine_steps=1 if prec == hp.HM_MIXED else 0)
+                          precision=prec, refine_steps=1 if prec == hp.HM_MIXED else 0,
+                          **engine_kw(args))
     t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
     sol.compute_scaling()
@@ -549,6 +555,7 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": workload_desc(w, sol.N, nrhs),
                    "precision": args.precision, "ordering": args.ordering,
+                   "engine": engine_kw(args) or "library defaults",
                    "l2": "inputs larger than L2 (alpha + far factors), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "alpha_entries": st["alpha_entries"], "far_entries": st["far_entries"],
@@ -616,6 +623,19 @@ def run_native(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def engine_kw(args):
+    """Engine switches of the mixed handle from the command line (defaults: the
+    library's)."""
+    kw = {}
+    if args.split_max:
+        kw["tc_split_max"] = args.split_max
+    if args.no_autotune:
+        kw["autotune"] = 0
+    if args.no_tensor_cores:
+        kw["tensor_cores"] = 0
+    return kw
 
 
 def kernel_table(prof, steps):
@@ -1042,7 +1062,7 @@ def run_large(args):
     t0 = time.perf_counter()
     sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=w.leaf_max, aca_tol=w.aca_tol,
                           ordering=hp.HM_ORDER_ND, fill=fill, precision=hp.HM_MIXED,
-                          refine_steps=1)
+                          refine_steps=1, **engine_kw(args))
     t_build = time.perf_counter() - t0
     t0 = time.perf_counter()
     sol.compute_scaling()

@@ -85,7 +85,12 @@ typedef struct {
                             process); that solve synchronises its stream, so
                             make it before any stream capture.  0 keeps the
                             built-in choice                                     */
-  int reserved[3];
+  int tc_split_max;      /* largest split-K size (inner rows) of a tensor-core
+                            sweep task, a power of two from 128; 0 (default):
+                            2048.  Shorter tasks keep shorter FP32 sums in
+                            tensor memory and hand more partial sums to the
+                            (IEEE FP32) finalize                                */
+  int reserved[2];
 } hm_params;
 
 /* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,

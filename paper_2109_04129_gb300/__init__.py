@@ -46,7 +46,8 @@ class hm_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("tensor_cores", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("term_tol", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("autotune", ctypes.c_int), ("tc_split_max", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double

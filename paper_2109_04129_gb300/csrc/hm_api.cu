@@ -87,6 +87,14 @@ const long long KMAX = 128;   // inner rows per split-K task of a sweep (more CT
 // measured on the 2-lambda sphere: mixed error 6.6-7.5e-5 with splits up to
 // 4096 rows against the 1e-4 bar)
 const long long KMAX_TC = 2048;
+long long split_cap(const hm_ctx* h) {
+  long long c = KMAX_TC;
+  if (h->p.tc_split_max >= (int)KMAX) {
+    c = KMAX;
+    while (c * 2 <= h->p.tc_split_max) c *= 2;
+  }
+  return c;
+}
 
 template <class T>
 hm_status upload(T** dptr, const std::vector<T>& v, size_t* bytes) {
@@ -380,7 +388,7 @@ void build_sweep_groups(hm_ctx* h, bool forward, Sweep& sw) {
         };
         constexpr long long TC_TASK_GOAL = 300;
         const long long goal = std::min(TC_TASK_GOAL, count(KMAX));
-        for (long long km = KMAX_TC; km > KMAX; km /= 2)
+        for (long long km = split_cap(h); km > KMAX; km /= 2)
           if (count(km) >= goal) {
             kmax = km;
             break;
@@ -1001,7 +1009,7 @@ hm_status tune_sweeps(hm_ctx* h, int nrhs) {
         long long best_k = pt.kmax;
         std::vector<std::pair<size_t, size_t>> seen{{sw->part[l].tasks.size(),
                                                      sw->fin[l].slots.size()}};
-        for (long long km = KMAX; km <= KMAX_TC; km *= 2) {
+        for (long long km = KMAX; km <= split_cap(h); km *= 2) {
           if (km == pt.kmax) continue;
           TaskList tl;
           FinList fl;
