@@ -89,7 +89,9 @@ typedef struct {
                             sweep task, a power of two from 128; 0 (default):
                             2048.  Shorter tasks keep shorter FP32 sums in
                             tensor memory and hand more partial sums to the
-                            (IEEE FP32) finalize                                */
+                            (IEEE FP32) finalize; they change the mixed
+                            chain's error little (its MMAs round each partial
+                            sum, which is as large as the whole)                */
   int reserved[2];
 } hm_params;
 

@@ -82,10 +82,14 @@ namespace {
 
 const long long KMAX = 128;   // inner rows per split-K task of a sweep (more CTAs on
                               // the narrow top levels of the elimination tree)
-// largest split size of the tensor-core sweeps: a task's FP32 sums in tensor
-// memory run over at most this many inner rows (longer sums cost accuracy;
-// measured on the 2-lambda sphere: mixed error 6.6-7.5e-5 with splits up to
-// 4096 rows against the 1e-4 bar)
+// largest split size of the tensor-core sweeps (the candidates the tuner
+// times run from KMAX up to this size).  The split size hardly moves the mixed
+// chain's error: on the 2-lambda sphere (one accumulator per task) it was
+// 6.1e-5 with splits of at most 128 rows and 6.6e-5 with 2048, because each
+// MMA's rounding scales with the partial sum, which is about as large in a
+// split as in the whole sum; the error follows the number of MMAs adding into
+// one accumulator, which the tensor-core kernel cuts with a separate
+// accumulator for the small slice products.
 const long long KMAX_TC = 2048;
 long long split_cap(const hm_ctx* h) {
   long long c = KMAX_TC;

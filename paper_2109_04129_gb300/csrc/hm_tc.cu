@@ -10,7 +10,8 @@
 //
 // Both operands are split into three bf16 slices (v = s0 + s1 + s2, about 24
 // significant bits) and the six slice products with s_p * s_q, p + q <= 2,
-// accumulate in FP32 in tensor memory: products carry FP32-level accuracy.
+// accumulate in FP32 in tensor memory (s0 * s0 and the rest in two separate
+// accumulators, added in the epilogue): products carry FP32-level accuracy.
 //
 // Operands: the matrix never changes between solves, so its three slices are
 // computed once at set-up (build_tc_tiles) and stored tile by tile in the
@@ -280,13 +281,27 @@ __device__ __forceinline__ int tc_nst(const GItem& I) {
 // Persistent, warp-specialised gather GEMM on complex64 lists.  Each CTA
 // walks its share of the tasks (costliest first) for one tile of 128 RHS:
 //   warp 0 (one thread) issues the 12 MMAs of a stage (6 slice products x 2 K
-//     steps) into the task's accumulator, tensor-memory half j & 1 for the
-//     CTA's j-th task, so the epilogue of one task overlaps the next task;
+//     steps) into the task's two accumulators: s0 x s0 into the main one, the
+//     five smaller slice products into a correction accumulator.  A narrow
+//     task (n_real <= 128) keeps both in tensor-memory half j & 1 for the
+//     CTA's j-th task, so the epilogue of one task overlaps the next task; a
+//     wide one (n_real <= 256) takes all 512 columns, and before task j the
+//     MMAs wait for the drain of task j - 2, or of j - 1 when j or j - 1 is
+//     wide;
 //   warp 1 (one thread) fetches the stage: the pre-split matrix tile and the
 //     16 input rows of every slice of the split panel (six bulk copies,
 //     completion on the stage's "tile" mbarrier);
-//   warps 2-5 read the accumulator (thread = TMEM lane = RHS row), add the
-//     base rows and store complex64 outputs.
+//   warps 2-5 read both accumulators (thread = TMEM lane = RHS row), add them
+//     and the base rows in FP32 and store complex64 outputs.
+// Why two accumulators: every MMA rounds the running FP32 sum it adds into
+// toward zero, and these sums cancel heavily, so the rounding error of a
+// chain grows with the number of MMAs that add into the same accumulator.
+// Five of the six products are 2^8 to 2^16 times smaller than s0 x s0: added
+// into the main sum they cost five roundings of it each for bits it barely
+// needs.  In a separate accumulator their roundings scale with their own
+// size, and the main sum takes one sixth of the MMAs (measured on the 2
+// lambda sphere: the mixed chain's error is unchanged by 16x shorter split-K
+// chains, so it is the count of MMAs per target, not the chain length).
 // Stage buffers form a ring of TC_RING: tile[b] full -> MMAs -> empty[b];
 // accumulators: tfull[h] (MMAs of a task done) -> epilogue -> tempty[h].
 // Every wait is bounded and watches a CTA-wide abort flag.
@@ -339,21 +354,25 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
     // ------------------------------------------------ MMA issuer (one thread)
     if (lane == 0) {
       int g = 0, j = 0;
-      bool stop = false;
+      bool stop = false, prev_wide = false;
       for (int u = blockIdx.x; u < n_tasks && !stop; u += gridDim.x) {
         const GTask t = tasks[order[u]];
         if (t.m <= 0) continue;
         const int n_real = tc_nreal(t.m);
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                ((uint32_t)(n_real >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-        const uint32_t dcol = tmem + (uint32_t)(j & 1) * 256u;
-        bool first = true;
+        const bool wide = n_real > 128;
+        const uint32_t dmain = tmem + (wide ? 0u : (uint32_t)(j & 1) * 256u);
+        const uint32_t dcorr = dmain + (wide ? 256u : 128u);
+        bool first_m = true, first_c = true;
         for (int it = t.it0; it < task_it_end(t) && !stop; ++it) {
           const int nst = tc_nst(items[it]);
           for (int st = 0; st < nst; ++st) {
-            // accumulator half j & 1 was last used by this CTA's task j - 2
-            if (first && j >= 2 &&
-                !tc_wait(b_tempty + 8u * (j & 1), (uint32_t)(((j - 2) >> 1) & 1), spin_limit,
+            // the columns of task j were last used by task j - 2 (both
+            // narrow), or by task j - 1 as well when either of the two is wide
+            const int need = (wide || prev_wide) ? j - 1 : j - 2;
+            if (first_m && need >= 0 &&
+                !tc_wait(b_tempty + 8u * (need & 1), (uint32_t)((need >> 1) & 1), spin_limit,
                          abortp, err)) {
               stop = true;
               break;
@@ -380,19 +399,26 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
                 for (int kh = 0; kh < TC_KR / 16; ++kh) {
                   const uint64_t da = da0 + (uint64_t)((p * A_SLICE_BYTES + kh * kstep) >> 4);
                   const uint64_t db = db0 + (uint64_t)((q * B_SLICE_BYTES + kh * 256) >> 4);
-                  const uint32_t acc = first ? 0u : 1u;
-                  first = false;
+                  // s0 x s0 into the main accumulator, the five smaller
+                  // products into a second one (see the note above)
+                  const bool mainp = p + q == 0;
+                  const uint32_t acc = (mainp ? first_m : first_c) ? 0u : 1u;
+                  if (mainp)
+                    first_m = false;
+                  else
+                    first_c = false;
                   asm volatile(
                       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                      :: "r"(dcol), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                      :: "r"(mainp ? dmain : dcorr), "l"(da), "l"(db), "r"(idesc), "r"(acc));
                 }
             tc_commit(b_empty + 8u * b);
             ++g;
           }
         }
-        if (!first && !stop) {
+        if (!first_m && !stop) {
           tc_commit(b_tfull + 8u * (j & 1));
+          prev_wide = wide;
           ++j;
         }
       }
@@ -479,23 +505,35 @@ __global__ void __launch_bounds__(TC_WTHREADS, 1) k_tc_gather(
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t half = (uint32_t)(j & 1) * 256u;
+      // main and correction sums: half j & 1 (at 0 and 128) for a narrow
+      // task, all of tensor memory (at 0 and 256) for a wide one
+      const bool wide = n_real > 128;
+      const uint32_t cm = wide ? 0u : (uint32_t)(j & 1) * 256u;
+      const uint32_t cc = cm + (wide ? 256u : 128u);
       for (int c0 = 0; c0 < n_real; c0 += 16) {
-        uint32_t v[16];
+        uint32_t v[16], w[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(lane_base + half + (uint32_t)c0));
+            : "r"(lane_base + cm + (uint32_t)c0));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+              "=r"(w[6]), "=r"(w[7]), "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]),
+              "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+            : "r"(lane_base + cc + (uint32_t)c0));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (col < nrhs) {
 #pragma unroll
           for (int jj = 0; jj < 16; jj += 2) {
             const int i = (c0 + jj) / 2;
             if (i < t.m) {
-              float2 yv = make_float2(__uint_as_float(v[jj]), __uint_as_float(v[jj + 1]));
+              float2 yv = make_float2(__uint_as_float(v[jj]) + __uint_as_float(w[jj]),
+                                      __uint_as_float(v[jj + 1]) + __uint_as_float(w[jj + 1]));
               if (base) {
                 const float2 bv = base[(long long)i * nrhs + col];
                 yv.x += bv.x;
