@@ -12,6 +12,11 @@ hm_power_series_solve over the whole RHS batch, inputs resident in HBM.
 N > 1 runs replicas (one independent copy of the system per GPU, RHS batch per
 GPU fixed: weak scaling, no collective on the data path).  Prints one JSON
 line on rank 0.
+
+Other workloads (--workload): sphere_r0.5_L3 and sphere_r2_L5_1rhs (one RHS),
+scatterer_batch (grouped solve of a seeded batch), sphere_scaling (set-up and
+solve time against N), sphere_r10_L7 (the 10-lambda sphere in RHS chunks) and
+leaf_size_study (series error against leaf size, Sec. V-A).
 """
 import argparse
 import json
@@ -1001,6 +1006,109 @@ def run_scaling(args):
         print(json.dumps(line), flush=True)
 
 
+LEAF_STUDY = (  # (icosphere level, radius in wavelengths, leaf caps, eta, reference)
+    (4, 1.0, (32, 64, 128, 256, 512, 1024), 0.0, "own"),
+    (4, 1.0, (64, 256), 1.0, "own"),
+    (5, 2.0, (128, 256, 512), 0.0, "first"),
+    (5, 2.0, (256,), 1.0, "first"),
+)
+
+
+def run_leaf_study(args):
+    """Accuracy of the power series against the leaf size (Sec. V-A, Fig. 4)
+    on the GPU: for each sphere, leaf cap and admissibility constant of
+    LEAF_STUDY, hm_build (ND order, reading A) and hm_compute_scaling, then
+    the x-polarised theta = 0 plane wave solved by the FP64 series with 2, 3
+    and 5 terms (the handle saved and loaded with each n_terms), the Eq. 45
+    ratio, and the relative L2 error against the direct solution of the
+    assembled H-matrix: Z applied to the identity in column chunks through
+    hm_apply (FP64-accurate products of a mixed handle; Z = Z^T) and solved by
+    a dense LU (torch.linalg.solve, the study's reference only).  "own": each
+    cap's own matrix; "first": the first cap's matrix for every cap of the
+    sphere (one LU; the matrices differ by the ACA tolerance)."""
+    import tempfile
+    import numpy as np
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from hm_workloads import icosphere
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rows = []
+    d = tempfile.mkdtemp()
+    path = os.path.join(d, "leaf.hmps")
+
+    def dense_z(sol, chunk=2048):
+        Zd = torch.empty((sol.N, sol.N), dtype=torch.complex128, device=dev)
+        for c0 in range(0, sol.N, chunk):
+            c = min(chunk, sol.N - c0)
+            E = torch.zeros((c, sol.N), dtype=torch.complex128, device=dev)
+            E[torch.arange(c, device=dev), torch.arange(c0, c0 + c, device=dev)] = 1.0
+            sol.apply("Z", Zd[c0:c0 + c], E)      # rows of Z^T = columns of Z
+            del E
+        torch.cuda.synchronize()
+        return Zd
+
+    try:
+        for level, radius, caps, eta, ref_kind in LEAF_STUDY:
+            v, f = icosphere(level, radius)
+            x_ref = None
+            for cap in caps:
+                t0 = time.perf_counter()
+                sol = hp.Solver.build(v, f, wavelength=1.0, leaf_max=cap, aca_tol=1e-4,
+                                      ordering=hp.HM_ORDER_ND, precision=hp.HM_MIXED,
+                                      refine_steps=1, eta=eta)
+                sol.compute_scaling()
+                t_setup = time.perf_counter() - t0
+                st = sol.stats()
+                b = torch.empty((1, sol.N), dtype=torch.complex128, device=dev)
+                sol.plane_wave(b, np.zeros(1), np.zeros(1), np.zeros(1, dtype=np.int32))
+                if x_ref is None or ref_kind == "own":
+                    Zd = dense_z(sol)
+                    x_ref = torch.linalg.solve(Zd, b[0].unsqueeze(1))[:, 0]
+                    resid = float((torch.linalg.vector_norm(Zd @ x_ref - b[0]) /
+                                   torch.linalg.vector_norm(b[0])).item())
+                    del Zd
+                    torch.cuda.empty_cache()
+                sol.save(path)
+                sol.close()
+                del sol
+                errs, ratio = {}, None
+                for nt in (2, 3, 5):
+                    s2 = hp.Solver.load(path, precision=hp.HM_FP64, n_terms=nt)
+                    X = torch.empty_like(b)
+                    s2.solve(X, b)
+                    if ratio is None:
+                        ratio = float(s2.diagnostics(1)[0][0])
+                    errs[f"err_{nt}_terms"] = float(
+                        (torch.linalg.vector_norm(X[0] - x_ref) /
+                         torch.linalg.vector_norm(x_ref)).item())
+                    s2.close()
+                os.unlink(path)
+                row = {"level": level, "radius_lambda": radius, "N": st["N"],
+                       "leaf_cap": cap, "eta": eta,
+                       "leaves": st["leaves"], "reference": ref_kind,
+                       "lu_residual": resid, "ratio_eq45": ratio, **errs,
+                       "setup_s": round(t_setup, 2)}
+                rows.append(row)
+                print(json.dumps({"partial": row}), file=sys.stderr, flush=True)
+                torch.cuda.empty_cache()
+    finally:
+        import shutil
+        shutil.rmtree(d, ignore_errors=True)
+    line = {"metric": "relative L2 error of the power-series solution against the direct "
+                      "solution vs leaf size (Sec. V-A, Fig. 4)",
+            "value": None, "unit": "relative L2 error", "n_gpus": ws, "steps": 1, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "icospheres 1 lambda (L4) and 2 lambda (L5), x-polarised "
+                                   "theta=0 plane wave, ACA 1e-4, ND order, reading A",
+                       "reference": "dense LU of the assembled H-matrix (torch.linalg.solve)"},
+            "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def batch_accuracy(sols, Xs, Bs, ws_list, bar=1e-4):
     """Each scatterer's grouped mixed result against the FP64 chain with the
     same refinement on the same set-up: the mixed handle is saved (H-matrix,
@@ -1214,6 +1322,8 @@ def dispatch(args):
         run_large(args)
     elif args.workload == "sphere_scaling":
         run_scaling(args)
+    elif args.workload == "leaf_size_study":
+        run_leaf_study(args)
     elif args.workload == "scatterer_batch":
         run_batch(args)
     else:

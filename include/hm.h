@@ -55,7 +55,7 @@ enum { HM_FILL_FULL = 0,   /* scaling keeps every fill-in block (Eq. 23 exact) *
        HM_FILL_NEAR = 1 }; /* fill restricted to the near-field pattern      */
 
 typedef struct {
-  double wavelength;     /* metres; k = 2 pi / wavelength                     */
+  double wavelength;     /* metres; k = 2 pi / wavelength (or see freq_hz)    */
   int leaf_max;          /* octree leaf cap in unknowns (Sec. II, V-A)         */
   int ordering;          /* HM_ORDER_*: elimination order of the leaves        */
   double aca_tol;        /* ACA / recompression tolerance eps of Eq. 12        */
@@ -92,12 +92,27 @@ typedef struct {
                             (IEEE FP32) finalize; they change the mixed
                             chain's error little (its MMAs round each partial
                             sum, which is as large as the whole)                */
+  double eta;            /* admissibility of two octree cells (Eq. 10) in
+                            hm_build: 0 (default) = far exactly when the cells
+                            do not touch (no shared face, edge or vertex); > 0 =
+                            far when they do not touch and
+                            min(diam) <= eta * dist, diam the cell diagonal and
+                            dist the distance between the two cubes, evaluated
+                            exactly on integer cell coordinates
+                            (3 min(edge)^2 <= eta^2 sum(gap^2)).  eta >= sqrt 3
+                            gives the non-touching partition; smaller eta moves
+                            pairs from far to near.  hm_import takes the blocks
+                            of its file and ignores it                          */
+  double freq_hz;        /* > 0: the frequency in Hz; hm_build then uses
+                            wavelength = 299 792 458 / freq_hz (metres) in place
+                            of the wavelength field.  0 (default): wavelength  */
   int reserved[2];
 } hm_params;
 
 /* Fill *p with the defaults: wavelength 1, leaf_max 64, DFS order, eps 1e-4,
  * full fill, 2 terms, FP64, no refinement, spin_limit 1<<26, tensor_cores 1,
- * fp64_emulation 1, term_tol 0 (fixed term count), autotune 1. */
+ * fp64_emulation 1, term_tol 0 (fixed term count), autotune 1, eta 0
+ * (non-touching admissibility), freq_hz 0. */
 void hm_default_params(hm_params* p);
 
 /* Build the H-matrix of a closed or open triangulated PEC surface (Sec. II:

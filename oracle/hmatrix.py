@@ -130,13 +130,15 @@ def _far_task(args):
 
 
 def build_hmatrix(verts, tris, wavelength=1.0, leaf_max=64, aca_tol=1e-4,
-                  processes=None, use_c=False):
-    """Fill the H-matrix of a mesh.  ``processes`` > 1 runs the block fills in
+                  processes=None, use_c=False, eta=0.0):
+    """Fill the H-matrix of a mesh.  ``eta`` > 0 adds the paper's form of the
+    admissibility (Eq. 10, see oracle.octree) to the non-touching test.
+    ``processes`` > 1 runs the block fills in
     a spawn-started process pool (same arithmetic, block by block);
     ``use_c`` evaluates the entries with the plain-C statement of the same
     formulas (oracle/cefie.c) instead of NumPy."""
     rwg = build_rwg(verts, tris)
-    tree = Octree(rwg.centre, leaf_max)
+    tree = Octree(rwg.centre, leaf_max) if not eta else Octree(rwg.centre, leaf_max, eta)
     near_u, far_u = tree.upper_blocks()
     P = tree.perm
     off = tree.leaf_off

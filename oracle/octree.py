@@ -14,6 +14,12 @@ eta of Eq. 10 open):
   * admissible = the two cells do not touch (no shared face, edge or vertex),
     tested exactly on integer cell coordinates; this yields the 26-neighbour
     near field the complexity analysis assumes (Sec. IV);
+  * with a constant eta > 0, Eq. 10 in the paper's form on top of that:
+    admissible when the cells do not touch and min(diam) <= eta dist, diam
+    the cell diagonal (sqrt 3 edge) and dist the distance between the two
+    cubes, evaluated exactly on the integer cell coordinates as
+    3 min(edge)^2 <= eta^2 sum(gap^2) (so ties, e.g. a one-cell diagonal gap
+    at eta = 1, are far);
   * block recursion from (root, root): admissible -> far; two leaves -> near;
     otherwise split the non-leaf side(s).
 
@@ -38,9 +44,10 @@ class Node:
 
 
 class Octree:
-    def __init__(self, points, leaf_max):
+    def __init__(self, points, leaf_max, eta=0.0):
         pts = np.asarray(points, dtype=np.float64)
         self.leaf_max = int(leaf_max)
+        self.eta = float(eta or 0.0)
         lo = pts.min(axis=0)
         hi = pts.max(axis=0)
         centre = (lo + hi) / 2.0
@@ -99,6 +106,25 @@ class Octree:
                 return False
         return True
 
+    def near_pair(self, s, t):
+        """Not admissible: the cells touch or, for eta > 0, fail
+        min(diam) <= eta dist (Eq. 10), on exact integer coordinates."""
+        if self.touching(s, t):
+            return True
+        if self.eta <= 0.0:
+            return False
+        a, b = self.nodes[s], self.nodes[t]
+        sa = 1 << (MAX_DEPTH - a.level)
+        sb = 1 << (MAX_DEPTH - b.level)
+        D = 0
+        for ax in range(3):
+            lo_a, hi_a = a.ijk[ax] * sa, (a.ijk[ax] + 1) * sa
+            lo_b, hi_b = b.ijk[ax] * sb, (b.ijk[ax] + 1) * sb
+            g = max(0, lo_b - hi_a, lo_a - hi_b)
+            D += g * g
+        m = float(min(sa, sb))
+        return not (3.0 * m * m <= (self.eta * self.eta) * float(D))
+
     def blocks(self):
         """Return (near, far): near = list of (leaf_i, leaf_j) over all ordered
         pairs; far = list of (node_s, node_t) over all ordered pairs."""
@@ -106,7 +132,7 @@ class Octree:
         stack = [(0, 0)]
         while stack:
             s, t = stack.pop()
-            if not self.touching(s, t):
+            if not self.near_pair(s, t):
                 far.append((s, t))
                 continue
             ns, nt = self.nodes[s], self.nodes[t]

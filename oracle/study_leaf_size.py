@@ -24,23 +24,16 @@ import numpy as np
 
 
 def eta_octree(eta):
-    """Octree whose admissibility is the paper's form with constant eta
-    (Eq. 10): cells s, t are far when min(diam_s, diam_t) <= eta dist(s, t),
-    diam the cell diagonal and dist the distance between the cells, and
-    never when they touch.  For the study only; the oracle and the GPU
-    library use non-touching admissibility."""
-    import math
+    """Octree whose admissibility adds the paper's form with constant eta
+    (Eq. 10): cells s, t are far when they do not touch and
+    min(diam_s, diam_t) <= eta dist(s, t), diam the cell diagonal and dist
+    the distance between the cells, on exact integer cell coordinates (the
+    oracle's and the GPU library's `eta`, see oracle.octree)."""
     from .octree import Octree
 
     class EtaOctree(Octree):
-        def touching(self, s, t):          # True = not admissible (near)
-            a, b = self.nodes[s], self.nodes[t]
-            ca, cb = self.size / 2 ** a.level, self.size / 2 ** b.level
-            lo_a = self.origin + np.array(a.ijk) * ca
-            lo_b = self.origin + np.array(b.ijk) * cb
-            gap = np.maximum(0.0, np.maximum(lo_b - (lo_a + ca), lo_a - (lo_b + cb)))
-            dist = float(np.linalg.norm(gap))
-            return not (dist > 0.0 and math.sqrt(3.0) * min(ca, cb) <= eta * dist)
+        def __init__(self, points, leaf_max):
+            super().__init__(points, leaf_max, eta)
 
     return EtaOctree
 

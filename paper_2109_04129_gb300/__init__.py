@@ -47,6 +47,7 @@ class hm_params(ctypes.Structure):
                 ("spin_limit", ctypes.c_longlong), ("tensor_cores", ctypes.c_int),
                 ("fp64_emulation", ctypes.c_int), ("term_tol", ctypes.c_double),
                 ("autotune", ctypes.c_int), ("tc_split_max", ctypes.c_int),
+                ("eta", ctypes.c_double), ("freq_hz", ctypes.c_double),
                 ("reserved", ctypes.c_int * 2)]
 
 

@@ -4,7 +4,8 @@
 //  hm_build: RWG basis (one unknown per interior edge, sorted edge keys, T+
 //    the lower triangle), octree over edge midpoints (split while > leaf_max,
 //    upper half on >= centre, Morton child order, depth-first leaves),
-//    non-touching admissibility on integer cell coordinates (Eq. 10 reading),
+//    non-touching admissibility on integer cell coordinates (Eq. 10 reading;
+//    hm_params.eta > 0 adds the min(diam) <= eta dist form on the same integers),
 //    dense near blocks filled on the GPU, far blocks by partially pivoted ACA
 //    on the GPU (Eq. 11-12) and QR/SVD recompression on the host.
 //  hm_compute_scaling: for k in elimination order D_k = Z~_kk, D_k^-1 by
@@ -110,6 +111,7 @@ struct Octree {
   double origin[3], size;
   const double* pts;
   int leaf_max;
+  double eta = 0.0;       // admissibility constant of Eq. 10 (0: non-touching)
 
   int build(std::vector<int>& idx, int level, const int ijk[3]) {
     int nid = (int)nodes.size();
@@ -154,9 +156,30 @@ struct Octree {
     }
     return true;
   }
+  // far pair: the cells do not touch and, for eta > 0, min(diam) <= eta dist
+  // (Eq. 10; diam = sqrt 3 edge, dist = distance between the cubes), tested
+  // as 3 min(edge)^2 <= eta^2 sum(gap^2) in units of the finest cell (the
+  // squares are exact integers, so ties such as a one-cell diagonal gap at
+  // eta = 1 fall on the far side on every machine)
+  bool admissible(int s, int t) const {
+    if (touching(s, t)) return false;
+    if (!(eta > 0.0)) return true;
+    const Node& a = nodes[s];
+    const Node& b = nodes[t];
+    long long sa = 1LL << (MAX_DEPTH - a.level), sb = 1LL << (MAX_DEPTH - b.level);
+    long long D = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+      long long la = a.ijk[ax] * sa, ha = (a.ijk[ax] + 1) * sa;
+      long long lb = b.ijk[ax] * sb, hb = (b.ijk[ax] + 1) * sb;
+      long long g = std::max(0LL, std::max(lb - ha, la - hb));
+      D += g * g;
+    }
+    const double m = (double)std::min(sa, sb);
+    return 3.0 * m * m <= (eta * eta) * (double)D;
+  }
 };
 
-void make_octree(const std::vector<double>& cen, int leaf_max, Octree& T) {
+void make_octree(const std::vector<double>& cen, int leaf_max, double eta, Octree& T) {
   int N = (int)(cen.size() / 3);
   double lo[3], hi[3];
   for (int a = 0; a < 3; ++a) {
@@ -178,6 +201,7 @@ void make_octree(const std::vector<double>& cen, int leaf_max, Octree& T) {
   T.size = 2.0 * half;
   T.pts = cen.data();
   T.leaf_max = leaf_max;
+  T.eta = eta;
   std::vector<int> idx(N);
   std::iota(idx.begin(), idx.end(), 0);
   int z[3] = {0, 0, 0};
@@ -591,7 +615,10 @@ hm_status hm_build(const double* verts, int nv, const int* tris, int nt, const h
   try {
     h = new hm_ctx();
     if (p) h->p = *p; else hm_default_params(&h->p);
-    if (h->p.leaf_max < 1 || !(h->p.wavelength > 0) || !(h->p.aca_tol > 0)) throw HM_ERR_INVALID;
+    if (h->p.freq_hz > 0) h->p.wavelength = 299792458.0 / h->p.freq_hz;
+    if (h->p.leaf_max < 1 || !(h->p.wavelength > 0) || !(h->p.aca_tol > 0) ||
+        !(h->p.eta >= 0) || !(h->p.freq_hz >= 0))
+      throw HM_ERR_INVALID;
     cudaGetDevice(&h->dev);
     Rwg rw;
     hm_status s = build_rwg(verts, nv, tris, nt, rw);
@@ -601,7 +628,7 @@ hm_status hm_build(const double* verts, int nv, const int* tris, int nt, const h
     h->wavelength = h->p.wavelength;
     h->k = 2.0 * 3.141592653589793 / h->p.wavelength;
     Octree T;
-    make_octree(rw.cen, h->p.leaf_max, T);
+    make_octree(rw.cen, h->p.leaf_max, h->p.eta, T);
     // block partition from (root, root)
     std::vector<std::pair<int, int>> near, far;
     std::vector<std::pair<int, int>> st{{0, 0}};
@@ -609,7 +636,7 @@ hm_status hm_build(const double* verts, int nv, const int* tris, int nt, const h
       auto pr = st.back();
       st.pop_back();
       int a = pr.first, b = pr.second;
-      if (!T.touching(a, b)) { far.push_back(pr); continue; }
+      if (T.admissible(a, b)) { far.push_back(pr); continue; }
       const Node& na = T.nodes[a];
       const Node& nb = T.nodes[b];
       if (na.leaf >= 0 && nb.leaf >= 0) near.push_back({na.leaf, nb.leaf});

@@ -153,3 +153,56 @@ def test_singular_diagonal_block_reported():
     with pytest.raises(hp.HMError) as e:
         sol.compute_scaling()
     assert e.value.status == hp.HM_ERR_SINGULAR
+
+
+@pytest.mark.parametrize("eta", [1.0, 2.0])
+def test_native_eta_admissibility(eta, tmp_path):
+    """hm_params.eta (Eq. 10, min(diam) <= eta dist on the cell cubes): the
+    GPU block partition equals the oracle's octree with the same eta, and the
+    whole pipeline meets the oracle's own build with that eta (FP64, 1e-4 as
+    for the default partition: independent ACA pivots)."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    from oracle.hmatrix import build_hmatrix
+    w = hw.get_workload("sphere_r0.5_L3")
+    v, f = w.build_mesh()
+    T = Octree(build_rwg(v, f).centre, 64, eta)
+    near_u, far_u = T.upper_blocks()
+    sol = hp.Solver.build(v, f, wavelength=w.wavelength, leaf_max=64, aca_tol=w.aca_tol, eta=eta)
+    p = str(tmp_path / "eta.hmps")
+    sol.save(p)
+    d = read_blocks(p)
+    assert sorted(d["near"]) == sorted(near_u)
+    geom = [(T.nodes[s].start, T.nodes[s].count, T.nodes[t].start, T.nodes[t].count)
+            for s, t in far_u]
+    assert [tuple(x[1:5]) for x in d["far"]] == geom
+    n0, _ = Octree(build_rwg(v, f).centre, 64).upper_blocks()
+    assert set(n0) < set(near_u)                 # eta < sqrt 3: more near pairs
+    sol.compute_scaling()
+    H = build_hmatrix(v, f, w.wavelength, 64, w.aca_tol, eta=eta)
+    S = compute_scaling(H, "A")
+    th, ph, po = w.angles()
+    B = EFIE(H.rwg, w.wavelength).plane_wave(th, ph, po)
+    Bd = to_dev(B)
+    X = torch.empty_like(Bd)
+    sol.solve(X, Bd)
+    want, _ = series_solve(H, S, B, 2)
+    assert rel(from_dev(X), want).max() < 1e-4
+
+
+def test_freq_hz_gives_the_wavelength(tmp_path):
+    """freq_hz = c0 / lambda builds the same system as wavelength = lambda
+    (lambda = 1 m: c0 / freq_hz is exact)."""
+    import torch
+    import paper_2109_04129_gb300 as hp
+    v, f = hw.icosphere(2, 0.25)
+    a = hp.Solver.build(v, f, wavelength=1.0, leaf_max=32)
+    b = hp.Solver.build(v, f, wavelength=123.0, freq_hz=299792458.0, leaf_max=32)
+    pa, pb = str(tmp_path / "a.hmps"), str(tmp_path / "b.hmps")
+    a.save(pa)
+    b.save(pb)
+    da, db = read_blocks(pa), read_blocks(pb)
+    assert da["wavelength"] == db["wavelength"] == 1.0
+    assert all(np.array_equal(da["near"][k], db["near"][k]) for k in da["near"])
+    with pytest.raises(hp.HMError):
+        hp.Solver.build(v, f, leaf_max=32, eta=-1.0)

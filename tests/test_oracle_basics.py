@@ -175,6 +175,38 @@ def test_octree_tiling_and_admissibility():
         assert np.all(pts >= lo - 1e-12) and np.all(pts <= lo + cell + 1e-12)
 
 
+def test_eta_admissibility_closed_forms():
+    """Eq. 10 with constant eta, min(diam) <= eta dist, on cells whose
+    diagonals and gaps are known in closed form (diam = sqrt 3 edge):
+    * two cells of edge c one cell apart diagonally: dist = sqrt 3 c = diam,
+      far exactly when eta >= 1 (the tie at eta = 1 is far);
+    * a face-neighbour of the neighbour (gap c along one axis): dist = c,
+      far exactly when eta >= sqrt 3;
+    * a cell of edge c one cell away from a cell of edge 2c: min diam is the
+      small one's; touching cells are near for every eta."""
+    import math
+    from oracle.octree import MAX_DEPTH, Node
+
+    def pair(cells, eta):
+        T = Octree.__new__(Octree)
+        T.eta = eta
+        T.nodes = [Node(level, ijk, 0, 1) for level, ijk in cells]
+        return not T.near_pair(0, 1)            # True = far
+
+    diag = [(3, (0, 0, 0)), (3, (2, 2, 2))]
+    assert pair(diag, 1.0) and not pair(diag, 1.0 - 1e-9)
+    axis = [(3, (0, 0, 0)), (3, (2, 0, 0))]
+    r3 = math.sqrt(3.0)
+    assert pair(axis, r3 * (1 + 1e-12)) and not pair(axis, r3 * (1 - 1e-12))
+    mixed = [(2, (0, 0, 0)), (3, (3, 0, 0))]     # big cell [0,2), small [3,4): gap 1 small edge
+    assert pair(mixed, 2.0) and not pair(mixed, 1.7)
+    touch = [(3, (0, 0, 0)), (3, (1, 1, 1))]
+    assert not pair(touch, 1e6) and not pair(touch, 0.0)
+    # eta = 0 is the plain non-touching test
+    assert pair(axis, 0.0) and pair(diag, 0.0)
+    assert MAX_DEPTH >= 3
+
+
 def test_aca_bounds_and_exact_rank():
     rng = np.random.default_rng(3)
     # explicit rank-5 complex matrix is recovered to rounding
