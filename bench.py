@@ -836,7 +836,6 @@ def run_batch(args):
     t_seq, v_seq = job_rate(ws, nrhs_tot, e0.elapsed_time(e1) / 1e3 / args.steps, dev)
     same = all(torch.equal(X, Y) for X, Y in zip(Xs, Ys))
     ratio_max = max(float(np.max(s.diagnostics(B.shape[0])[0])) for s, B in zip(sols, Bs))
-    accuracy = batch_accuracy(sols, Xs, Bs, ws_list) if prec == hp.HM_MIXED else None
     # per-kernel timing: one profiled pass of the single solves (events around
     # every launch cannot be recorded in the graph)
     tot = {}
@@ -888,6 +887,12 @@ def run_batch(args):
         e2e_step()
     t_e2e, v_e2e = job_rate(ws, nrhs_tot, (time.perf_counter() - t0) / args.steps, dev)
     nbytes = sum(B.numel() * 16 for B in Bs)
+    n_handles = len(sols)
+    # accuracy last: it closes every mixed handle once its comparator is done
+    # (all handles resident leave no room for the FP64 comparators)
+    del Ys, Bh, Xh, Bd
+    torch.cuda.empty_cache()
+    accuracy = batch_accuracy(sols, Xs, Bs, ws_list) if prec == hp.HM_MIXED else None
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_dev,
@@ -895,7 +900,7 @@ def run_batch(args):
         "dtype": "c128" if prec == hp.HM_FP64 else
                  "mixed: c64 chain on tcgen05, c128 D^-1, FP64-accurate residual",
         "data": "synthetic",
-        "config": {"workload": f"scatterer_batch: {len(sols)} seeded closed scatterers "
+        "config": {"workload": f"scatterer_batch: {n_handles} seeded closed scatterers "
                                f"(sphere / prolate ellipsoid / closed cylinder), N "
                                f"{min(Ns)}-{max(Ns)} (total {sum(Ns)}), leaves 32-256, "
                                f"91 monostatic RHS each ({nrhs_tot} total)",
@@ -1112,9 +1117,10 @@ def run_leaf_study(args):
 def batch_accuracy(sols, Xs, Bs, ws_list, bar=1e-4):
     """Each scatterer's grouped mixed result against the FP64 chain with the
     same refinement on the same set-up: the mixed handle is saved (H-matrix,
-    scaling and supernodes, FP64 values) and loaded as an FP64 handle, one
-    scatterer at a time.  Returns the largest relative L2 error over all RHS
-    and the scatterers whose error exceeds the bar."""
+    scaling and supernodes, FP64 values), closed, and loaded as an FP64
+    handle, one scatterer at a time (the mixed handles are closed here, so
+    this comes last).  Returns the largest relative L2 error over all RHS and
+    the scatterers whose error exceeds the bar."""
     import tempfile
     import numpy as np
     import torch
@@ -1123,18 +1129,21 @@ def batch_accuracy(sols, Xs, Bs, ws_list, bar=1e-4):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "s.hmps")
         for i, (sol, X, B) in enumerate(zip(sols, Xs, Bs)):
+            ratio = float(np.max(sol.diagnostics(B.shape[0])[0]))
+            n = sol.N
             sol.save(path)
+            sol.close()
+            torch.cuda.empty_cache()
             ref = hp.Solver.load(path, precision=hp.HM_FP64, refine_steps=1)
             Xr = torch.empty_like(B)
             ref.solve(Xr, B)
             torch.cuda.synchronize()
             e = float((torch.linalg.vector_norm(X - Xr, dim=1) /
                        torch.linalg.vector_norm(Xr, dim=1)).max().item())
-            ratio = float(np.max(sol.diagnostics(B.shape[0])[0]))
             per.append(round(e, 9))
             worst = max(worst, e)
             if e > bar:
-                over.append({"scatterer": ws_list[i].name, "N": sol.N, "rel_err": e,
+                over.append({"scatterer": ws_list[i].name, "N": n, "rel_err": e,
                              "series_ratio_max": ratio})
             ref.close()
             del Xr

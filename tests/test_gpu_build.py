@@ -176,8 +176,11 @@ def test_native_eta_admissibility(eta, tmp_path):
     geom = [(T.nodes[s].start, T.nodes[s].count, T.nodes[t].start, T.nodes[t].count)
             for s, t in far_u]
     assert [tuple(x[1:5]) for x in d["far"]] == geom
-    n0, _ = Octree(build_rwg(v, f).centre, 64).upper_blocks()
-    assert set(n0) < set(near_u)                 # eta < sqrt 3: more near pairs
+    n0, f0 = Octree(build_rwg(v, f).centre, 64).upper_blocks()
+    if eta < 3 ** 0.5:
+        assert set(n0) < set(near_u)             # eta < sqrt 3: more near pairs
+    else:
+        assert n0 == near_u and f0 == far_u      # eta >= sqrt 3: the non-touching partition
     sol.compute_scaling()
     H = build_hmatrix(v, f, w.wavelength, 64, w.aca_tol, eta=eta)
     S = compute_scaling(H, "A")
