@@ -69,6 +69,72 @@ def static_potentials(obs, tri):
     return I_s, I_v, rho
 
 
+def static_gradient(obs, tri):
+    """obs: (P, 3); tri: (P, 3, 3).  Returns int_T (r - r') / R^3 ds' (P, 3),
+    the static kernel of the MFIE's K operator (minus the gradient of the
+    1/R potential above), in the same edge quantities:
+      int_T (r - r')/R^3 ds' = sum_i uhat_i f_i + sign(h) nhat sum_i beta_i
+    (in-plane part from the edge logarithms, normal part the solid angle the
+    triangle subtends at r).  At h = 0 the normal part is zero (principal
+    value); the in-plane part is singular on the triangle's edges only.
+
+    Pinned by: brute-force Gauss-Legendre quadrature on the collapsed square
+    at points above, below and beside the triangle (gradient_brute), and
+    the finite-difference gradient of static_potentials' int 1/R."""
+    obs = np.asarray(obs, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.float64)
+    p0, p1, p2 = tri[:, 0], tri[:, 1], tri[:, 2]
+    n = np.cross(p1 - p0, p2 - p0)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    h = np.einsum("pc,pc->p", n, obs - p0)
+    rho = obs - h[:, None] * n
+    ah = np.abs(h)
+    out = np.zeros((len(obs), 3))
+    bsum = np.zeros(len(obs))
+    for pa, pb in ((p0, p1), (p1, p2), (p2, p0)):
+        e = pb - pa
+        elen = np.linalg.norm(e, axis=1)
+        lhat = e / elen[:, None]
+        uhat = np.cross(lhat, n)
+        lp = np.einsum("pc,pc->p", pb - rho, lhat)
+        lm = np.einsum("pc,pc->p", pa - rho, lhat)
+        t = np.einsum("pc,pc->p", pa - rho, uhat)
+        R0sq = t * t + h * h
+        Rp = np.sqrt(R0sq + lp * lp)
+        Rm = np.sqrt(R0sq + lm * lm)
+        degenerate = R0sq <= (1e-14 * elen) ** 2
+        with np.errstate(divide="ignore", invalid="ignore"):
+            f_pos = np.log((Rp + lp) / (Rm + lm))
+            f_neg = np.log((Rm - lm) / (Rp - lp))
+            beta = (np.arctan(t * lp / (R0sq + ah * Rp)) -
+                    np.arctan(t * lm / (R0sq + ah * Rm)))
+        f = np.where(lm + lp >= 0.0, f_pos, f_neg)
+        f = np.where(degenerate, 0.0, f)
+        beta = np.where(degenerate, 0.0, beta)
+        out += uhat * f[:, None]
+        bsum += beta
+    out += (np.sign(h) * bsum)[:, None] * n
+    return out
+
+
+def gradient_brute(obs, tri, order=200):
+    """Brute-force reference for int_T (r - r')/R^3 ds' at one point off the
+    triangle: the collapsed-square map r' = p0 + u (p1 - p0) + u v (p2 - p1)
+    (Jacobian 2 A u) with an order x order Gauss-Legendre rule.  Tests only."""
+    obs = np.asarray(obs, dtype=np.float64)
+    p0, p1, p2 = np.asarray(tri, dtype=np.float64)
+    x, w = np.polynomial.legendre.leggauss(order)
+    x = 0.5 * (x + 1.0)
+    w = 0.5 * w
+    U, V = np.meshgrid(x, x, indexing="ij")
+    W = np.outer(w, w)
+    area2 = np.linalg.norm(np.cross(p1 - p0, p2 - p0))
+    r = p0 + U[..., None] * (p1 - p0) + (U * V)[..., None] * (p2 - p1)
+    d = obs - r
+    R = np.linalg.norm(d, axis=-1)
+    return np.einsum("uv,uvc->c", W * U * area2 / R ** 3, d)
+
+
 def duffy_brute(obs, tri, order=48):
     """Brute-force reference for (I_s, I_v) at one point: split the triangle at
     the projection rho into three sub-triangles with apex rho, map each to the

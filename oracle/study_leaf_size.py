@@ -13,6 +13,7 @@ matrices differ only by the ACA tolerance).
     python -m oracle.study_leaf_size --level 4 --radius 1.0 --caps 32 64 128 256 512 1024
     python -m oracle.study_leaf_size --level 4 --radius 1.0 --caps 64 256 --eta 1
     python -m oracle.study_leaf_size --level 4 --radius 1.0 --binary 0.25 0.5 1.0 --eta 1
+    python -m oracle.study_leaf_size --level 5 --radius 2.0 --caps 128 256 --cfie 0.5
 
 prints one line per cap: leaves, leaf cell edge in wavelengths (min / median
 / max over the leaves), the Eq. 45 ratio ||it_1|| / ||it_0||, and the errors.
@@ -168,6 +169,10 @@ def main():
     ap.add_argument("--processes", type=int, default=None)
     ap.add_argument("--eta", type=float, default=None,
                     help="admissibility min(diam) <= eta dist instead of non-touching cells")
+    ap.add_argument("--cfie", type=float, default=None, metavar="ALPHA",
+                    help="the CFIE of Eq. 8 with this alpha instead of the EFIE (non-symmetric "
+                         "scaling, oracle.nonsym); reference: the LU of the full CFIE matrix, "
+                         "filled once for all caps")
     ap.add_argument("--binary", type=float, nargs="+", default=None, metavar="LEAF_SIZE",
                     help="the paper's binary tree with these leaf sizes (wavelengths) "
                          "instead of octree caps; admissibility eta (default 1)")
@@ -180,6 +185,8 @@ def main():
         hmatrix.Octree = eta_octree(a.eta)
     v, f = icosphere(a.level, a.radius)
     procs = a.processes or default_processes()
+    if a.cfie is not None:
+        return cfie_study(a, v, f, procs)
     ref = None
     adm = f"eta {a.eta:g}" if a.eta is not None else "non-touching"
     tree = "binary tree, leaf size" if a.binary is not None else "octree, leaf cap"
@@ -202,6 +209,41 @@ def main():
         for nt in a.terms:
             X, rat = series_solve(H, S, B, nt)
             errs.append(float(rel_err(X, ref)[0]))
+            if ratio is None and rat.size:
+                ratio = float(rat[0, 0])
+        e = leaf_edges(H.tree, 1.0)
+        print(f"{cap} {H.n_leaves} {e.min():.3f} {np.median(e):.3f} {e.max():.3f} "
+              f"{ratio:.3f} " + " ".join(f"{x:.3e}" for x in errs)
+              + f" {time.perf_counter() - t0:.0f}", flush=True)
+
+
+def cfie_study(a, v, f, procs):
+    """The same sweep for the CFIE (Eq. 8, alpha = a.cfie): the full matrix
+    filled once, each cap's H-matrix cut from it (far blocks by truncated SVD
+    at the ACA tolerance), the non-symmetric scaling (reading A) and series,
+    against the LU of the full matrix."""
+    from .mfie import CFIE
+    from .nonsym import (compute_scaling_general, dense_cfie, hmatrix_from_dense,
+                         series_solve_general)
+    from .series import rel_err
+    t0 = time.perf_counter()
+    rwg, Zd = dense_cfie(v, f, 1.0, a.cfie, procs)
+    b = CFIE(rwg, 1.0, a.cfie).plane_wave([0.0], [0.0], [0])
+    x_ref = np.linalg.solve(Zd, b)
+    adm = f"eta {a.eta:g}" if a.eta is not None else "non-touching"
+    print(f"# icosphere L{a.level}, radius {a.radius} lambda, CFIE alpha {a.cfie}, octree, "
+          f"admissibility {adm}, reference LU of the full matrix "
+          f"(fill + LU {time.perf_counter() - t0:.0f} s)", flush=True)
+    print("# cap leaves edge_min edge_med edge_max ratio_eq45 "
+          + " ".join(f"err_{t}" for t in a.terms) + " seconds", flush=True)
+    for cap in a.caps:
+        t0 = time.perf_counter()
+        H = hmatrix_from_dense(Zd, rwg, int(cap), 1e-4, a.eta or 0.0)
+        S = compute_scaling_general(H, "A")
+        errs, ratio = [], None
+        for nt in a.terms:
+            X, rat = series_solve_general(H, S, b, nt)
+            errs.append(float(rel_err(X, x_ref)[0]))
             if ratio is None and rat.size:
                 ratio = float(rat[0, 0])
         e = leaf_edges(H.tree, 1.0)
