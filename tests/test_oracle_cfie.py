@@ -217,3 +217,24 @@ def test_cfie_series_limits():
     X1 = np.empty_like(xl1)
     X1[H1.perm] = xl1
     assert np.abs(x1 - X1).max() <= 1e-10 * np.abs(X1).max() and np.all(r1 == 0.0)
+
+
+def test_dense_fill_and_hmatrix_from_dense():
+    """The study path (one dense CFIE fill, by a spawned pool or serially,
+    then each cap's H-matrix cut from it) gives the same matrix and blocks
+    as the block-by-block build."""
+    from oracle.nonsym import dense_cfie, hmatrix_from_dense
+    v, f = hw.icosphere(2, 0.25)
+    r, Z1 = dense_cfie(v, f, 1.0, 0.5, processes=1)
+    _, Z2 = dense_cfie(v, f, 1.0, 0.5, processes=2)
+    scale = np.abs(Z1).max()
+    assert np.abs(Z1 - Z2).max() <= 1e-13 * scale
+    H = hmatrix_from_dense(Z1, r, 32)
+    _, _, Hb, _, _ = _cfie_small()
+    assert sorted(H.near) == sorted(Hb.near)
+    assert max(np.abs(H.near[k] - Hb.near[k]).max() for k in H.near) <= 1e-12 * scale
+    assert [x[:5] for x in H.far] == [x[:5] for x in Hb.far]
+    assert np.abs(H.to_dense() - Hb.to_dense()).max() <= 1e-12 * scale
+    # the far blocks keep the SVD tolerance against the full matrix
+    Zp = Z1[np.ix_(H.perm, H.perm)]
+    assert np.linalg.norm(H.to_dense() - Zp) <= 1e-4 * np.linalg.norm(Zp)
