@@ -47,8 +47,12 @@ typedef enum {
 } hm_status;
 
 enum { HM_FP64 = 0,        /* every product in complex FP64                   */
-       HM_MIXED = 1 };     /* scaling/far products in low precision with FP32
+       HM_MIXED = 1,       /* scaling/far products in low precision with FP32
                               accumulation, D^-1 in FP64, FP64 refinement     */
+       HM_MIXED_BF16 = 1 };/* the same mode by its operand type: the products
+                              are three-way bf16 slice products (about 24
+                              significant bits).  There is no TF32 mode: a
+                              tf32 operand keeps 10 mantissa bits             */
 enum { HM_ORDER_DFS = 0,   /* leaves in octree depth-first (Morton) order    */
        HM_ORDER_ND = 1 };  /* geometric nested dissection of the leaf graph  */
 enum { HM_FILL_FULL = 0,   /* scaling keeps every fill-in block (Eq. 23 exact) */

@@ -22,6 +22,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 HM_OK, HM_ERR_INVALID, HM_ERR_CUDA, HM_ERR_OOM, HM_ERR_SINGULAR = 0, 1, 2, 3, 4
 HM_ERR_TIMEOUT, HM_ERR_STATE, HM_ERR_IO, HM_WARN_SERIES_RATIO = 5, 6, 7, 100
 HM_FP64, HM_MIXED = 0, 1
+HM_MIXED_BF16 = HM_MIXED          # the mixed mode by its operand type (bf16 slice products)
 HM_ORDER_DFS, HM_ORDER_ND = 0, 1
 HM_FILL_FULL, HM_FILL_NEAR = 0, 1
 OPS = {"RT": 0, "R": 1, "DINV": 2, "FAR": 3, "NEAR": 4, "Z": 5}
