@@ -25,6 +25,14 @@ float64 pairs; every matrix row-major.
                  (group g = ranks grp[g] .. grp[g+1]-1), then for every group
                  with more than one leaf T_G = (I - A_G^T)^-1, complex128
                  [n_G * n_G] (oracle.scaling.supernode_inverse)
+    b"NONSYM01"  a non-symmetric system (the CFIE, oracle.nonsym): the main
+                 sections then hold the blocks of their own order only (near
+                 i <= j, far blocks whose row cluster starts first), applied
+                 without transposes, and this section the rest:
+                 int64 n; n x (int64 i, j (i > j); complex128 block[m_i * m_j]);
+                 int64 n; n far blocks as above (row cluster after column cluster);
+                 int64 has_left; if 1, per (k, j) in alpha's order the left
+                 coefficient alphaL_kj transposed, complex128 [m_elim[k] * m_elim[j]]
 
 Parity unpinned beyond the round trip: this is a file format, not arithmetic.
 """
@@ -95,6 +103,41 @@ def write_blocks(path, H, S=None, centres=True, groups=None):
                     f.write(_c(supernode_inverse(S, H.leaf_off, groups[g], groups[g + 1])))
 
 
+def write_blocks_nonsym(path, H, S=None):
+    """Block file of a non-symmetric H-matrix (oracle.nonsym.HMatrixGen) and
+    its left and right scaling (ScalingGen): the main sections with the upper
+    blocks and alpha, D^-1, then the NONSYM01 section."""
+    from types import SimpleNamespace
+    up_near = {ij: B for ij, B in H.near.items() if ij[0] <= ij[1]}
+    lo_near = {ij: B for ij, B in H.near.items() if ij[0] > ij[1]}
+    up_far = [b for b in H.far if b[1] < b[3]]
+    lo_far = [b for b in H.far if b[1] > b[3]]
+    assert len(up_far) + len(lo_far) == len(H.far)
+    Hup = SimpleNamespace(N=H.N, n_leaves=H.n_leaves, near=up_near, far=up_far, perm=H.perm,
+                          leaf_off=H.leaf_off, k=H.k, meta=H.meta)
+    write_blocks(path, Hup, S, centres=False)
+    with open(path, "ab") as f:
+        f.write(b"NONSYM01")
+        f.write(struct.pack("<q", len(lo_near)))
+        for (i, j) in sorted(lo_near):
+            f.write(struct.pack("<2q", i, j))
+            f.write(_c(lo_near[(i, j)]))
+        f.write(struct.pack("<q", len(lo_far)))
+        for kind, r0, mm, c0, n, P, Q in lo_far:
+            if kind == "lr":
+                f.write(struct.pack("<6q", 0, r0, mm, c0, n, P.shape[1]))
+                f.write(_c(P))
+                f.write(_c(Q))
+            else:
+                f.write(struct.pack("<6q", 1, r0, mm, c0, n, 0))
+                f.write(_c(P))
+        f.write(struct.pack("<q", 0 if S is None else 1))
+        if S is not None:
+            for k in range(S.n):
+                for j in S.rows[k]:
+                    f.write(_c(S.alphaL[(k, j)].T))
+
+
 def read_blocks(path):
     """Inverse of write_blocks -> dict of numpy arrays (tests only).  The file
     is memory-mapped: the arrays are read-only views of it."""
@@ -125,14 +168,15 @@ def read_blocks(path):
     for _ in range(nn):
         i, j = take("<2q")
         near[(i, j)] = arr("<c16", m[i] * m[j]).reshape(m[i], m[j])
-    far = []
-    for _ in range(nf):
+
+    def far_block():
         kind, r0, mm, c0, n, r = take("<6q")
         if kind == 0:
-            far.append(("lr", r0, mm, c0, n, arr("<c16", mm * r).reshape(mm, r),
-                        arr("<c16", n * r).reshape(n, r)))
-        else:
-            far.append(("dense", r0, mm, c0, n, arr("<c16", mm * n).reshape(mm, n), None))
+            return ("lr", r0, mm, c0, n, arr("<c16", mm * r).reshape(mm, r),
+                    arr("<c16", n * r).reshape(n, r))
+        return ("dense", r0, mm, c0, n, arr("<c16", mm * n).reshape(mm, n), None)
+
+    far = [far_block() for _ in range(nf)]
     out = dict(N=N, perm=perm, leaf_off=off, near=near, far=far, k=k,
                wavelength=wl, reading=reading)
     if has_s:
@@ -166,6 +210,20 @@ def read_blocks(path):
                     nG = int(np.sum(me[grp[g]:grp[g + 1]]))
                     T[g] = arr("<c16", nG * nG).reshape(nG, nG)
             out.update(groups=grp, T=T)
+        elif tag == b"NONSYM01":
+            (nlo,) = take("<q")
+            for _ in range(nlo):
+                i, j = take("<2q")
+                assert i > j
+                near[(i, j)] = arr("<c16", m[i] * m[j]).reshape(m[i], m[j])
+            (nfl,) = take("<q")
+            far.extend(far_block() for _ in range(nfl))
+            (has_l,) = take("<q")
+            if has_l:
+                me = m[out["elim"]]
+                out["alphaL"] = {(kk, j): arr("<c16", me[kk] * me[j]).reshape(me[kk], me[j]).T
+                                 for kk in range(nl) for j in out["rows"][kk]}
+            out["nonsym"] = True
         else:
             raise ValueError(f"unknown section {tag!r}")
     assert pos == len(buf)

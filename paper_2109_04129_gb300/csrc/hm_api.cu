@@ -112,6 +112,8 @@ hm_status upload(T** dptr, const std::vector<T>& v, size_t* bytes) {
 }
 
 hm_status upload_tasks(TaskList& tl, size_t* bytes) {
+  tl.abuf_mask = 0;
+  for (const GItem& it : tl.items) tl.abuf_mask |= 1u << it.a_buf;
   hm_status s = upload(&tl.d_tasks, tl.tasks, bytes);
   if (s != HM_OK) return s;
   return upload(&tl.d_items, tl.items, bytes);
@@ -202,7 +204,9 @@ void build_sweep(hm_ctx* h, bool forward, Sweep& sw) {
           long long ai = src[t][q].second;
           GItem it{};
           it.a_off = h->alpha_off[ai];
-          it.a_buf = AB_ALPHA;
+          // forward over a non-symmetric system: the left coefficient
+          // alphaL_st, stored as its transpose in alpha's layout
+          it.a_buf = (forward && h->nonsym) ? AB_ALPHAL : AB_ALPHA;
           if (forward) {   // alpha_st is m_s x m_t; need alpha^T: trans read
             it.lda = mt;
             it.trans = 1;
@@ -245,7 +249,8 @@ hm_status row_exponents(hm_ctx* h, const TaskList& tl, RowExp& R) {
       const GItem& it = tl.items[q];
       const std::vector<cplx>* src = it.a_buf == AB_NEAR ? &h->h_near
                                      : it.a_buf == AB_FAR ? &h->h_far
-                                     : it.a_buf == AB_ALPHA ? &h->h_alpha : &h->h_dinv;
+                                     : it.a_buf == AB_ALPHA ? &h->h_alpha
+                                     : it.a_buf == AB_ALPHAL ? &h->h_alphaL : &h->h_dinv;
       const cplx* A = src->data() + it.a_off;
       // a row segment of a stacked task covers its rows only
       const int i0 = it.nrow > 0 ? it.r0 : 0, i1 = it.nrow > 0 ? it.r0 + it.nrow : t.m;
@@ -525,7 +530,7 @@ hm_status build_schedules(hm_ctx* h) {
     const FarDesc& f = h->far[bi];
     if (f.kind != 0 || f.rank == 0) continue;
     by_input[{f.c0, f.n}].push_back(Seg{(int)bi, 0});
-    by_input[{f.r0, f.m}].push_back(Seg{(int)bi, 1});
+    if (!h->nonsym) by_input[{f.r0, f.m}].push_back(Seg{(int)bi, 1});
   }
   constexpr int SROWS = 128;                      // rows of a stacked task
   int nt = 0;
@@ -576,6 +581,7 @@ hm_status build_schedules(hm_ctx* h) {
       }
       share[l].push_back(f.m);
     }
+    if (h->nonsym) continue;        // a block of its own order only: no V U^T side
     for (int l = leaf_of(f.c0); l < n && h->leaf_off[l] < f.c0 + f.n; ++l) {
       long long dc = h->leaf_off[l] - f.c0;
       if (f.kind == 0) {
@@ -619,12 +625,13 @@ hm_status build_schedules(hm_ctx* h) {
     h->far2_tl.tasks.push_back(t);
   }
   split_wide_tasks(h->far2_tl, 128);
-  // near field Z_N (upper blocks + transposes)
+  // near field Z_N (upper blocks + transposes; every ordered block once for a
+  // non-symmetric system)
   std::vector<std::vector<GItem>> near_leaf(n);
   for (const NearDesc& d : h->near) {
     near_leaf[d.i].push_back(GItem{d.off, AB_NEAR, h->m[d.j], 0, h->m[d.j], VB_IN,
                                    (int)h->leaf_off[d.j]});
-    if (d.i != d.j)
+    if (d.i != d.j && !h->nonsym)
       near_leaf[d.j].push_back(GItem{d.off, AB_NEAR, h->m[d.j], 1, h->m[d.i], VB_IN,
                                      (int)h->leaf_off[d.i]});
   }
@@ -708,6 +715,7 @@ ABufs abufs(hm_ctx* h) {
   a.p[AB_ALPHA] = h->d_alpha;
   a.p[AB_DINV] = h->d_dinv;
   a.p[AB_TINV] = h->d_tinv;
+  a.p[AB_ALPHAL] = h->d_alphaL;
   return a;
 }
 
@@ -752,6 +760,7 @@ static void tables(hm_ctx* h, void* in, void* out, bool low, VBufs& v, ABufs& a)
   a.p[AB_ALPHA] = low ? mixed_alpha(h) : h->d_alpha;
   a.p[AB_DINV] = h->d_dinv;
   a.p[AB_TINV] = low ? mixed_tinv(h) : h->d_tinv;
+  a.p[AB_ALPHAL] = low ? nullptr : h->d_alphaL;   // FP64 only (non-symmetric handles)
 }
 
 hm_status ensure_err(hm_ctx* h) {
@@ -1197,6 +1206,7 @@ hm_status upload_values(hm_ctx* h) {
   if (!s) s = upload(&h->d_tinv, h->h_tinv, b);
   if (!s) s = upload(&h->d_alpha, h->h_alpha, b);
   if (!s) s = upload(&h->d_dinv, h->h_dinv, b);
+  if (!s && !h->h_alphaL.empty()) s = upload(&h->d_alphaL, h->h_alphaL, b);
   return s;
 }
 hm_status rebuild_schedules(hm_ctx* h) { return build_schedules(h); }
@@ -1283,7 +1293,7 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
       r.get(h->h_near.data() + d.off, cnt);
       h->near.push_back(d);
     }
-    for (long long b = 0; b < nf; ++b) {
+    auto read_far = [&]() {
       long long kind = r.q(), r0 = r.q(), m = r.q(), c0 = r.q(), n = r.q(), rank = r.q();
       if (!r.ok || kind < 0 || kind > 1 || r0 < 0 || c0 < 0 || m <= 0 || n <= 0 ||
           r0 + m > N || c0 + n > N || rank < 0 || rank > std::min(m, n))
@@ -1300,7 +1310,8 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
         r.get(h->h_far.data() + d.offU, (size_t)(m * n));
       }
       h->far.push_back(d);
-    }
+    };
+    for (long long b = 0; b < nf; ++b) read_far();
     if (has_s) {
       long long na = r.q();
       h->elim.resize(nl);
@@ -1393,10 +1404,40 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
         h->h_tinv.resize(nt_all);
         r.get(h->h_tinv.data(), h->h_tinv.size());
         if (!r.ok) throw std::runtime_error("supernodes");
+      } else if (memcmp(tag, "NONSYM01", 8) == 0) {
+        // non-symmetric system (the CFIE of Eq. 8): the near blocks below the
+        // diagonal, the far blocks whose row cluster follows their column
+        // cluster, and with the scaling the left coefficients alphaL_kj,
+        // each stored as its transpose in alpha's order and shapes
+        const long long nnl = r.q();
+        if (!r.ok || nnl < 0 || nnl > nl * nl) throw std::runtime_error("nonsym");
+        for (long long b = 0; b < nnl; ++b) {
+          long long i = r.q(), j = r.q();
+          if (!r.ok || j < 0 || i <= j || i >= nl) throw std::runtime_error("nonsym near");
+          NearDesc d{(int)i, (int)j, (long long)h->h_near.size()};
+          size_t cnt = (size_t)h->m[i] * h->m[j];
+          h->h_near.resize(h->h_near.size() + cnt);
+          r.get(h->h_near.data() + d.off, cnt);
+          h->near.push_back(d);
+        }
+        const long long nfl = r.q();
+        if (!r.ok || nfl < 0) throw std::runtime_error("nonsym far");
+        for (long long b = 0; b < nfl; ++b) read_far();
+        const long long has_l = r.q();
+        if (!r.ok || has_l != (h->has_scaling ? 1 : 0)) throw std::runtime_error("nonsym alphaL");
+        if (has_l) {
+          h->h_alphaL.resize(h->h_alpha.size());
+          r.get(h->h_alphaL.data(), h->h_alphaL.size());
+        }
+        if (!r.ok) throw std::runtime_error("nonsym");
+        h->nonsym = true;
       } else {
         throw std::runtime_error("section");
       }
     }
+    // a non-symmetric system runs the FP64 chain on the leaf-level sweeps (the
+    // supernode products and the mixed engines are written for Z = Z^T)
+    if (h->nonsym && (!h->grp.empty() || h->p.precision != HM_FP64)) throw HM_ERR_INVALID;
     fclose(f);
     f = nullptr;
     s = upload_values(h);
@@ -1424,6 +1465,7 @@ hm_status hm_import(const char* path, const hm_params* p, hm_handle* out) {
 
 hm_status hm_save(hm_handle h, const char* path) {
   if (!h || !path) return HM_ERR_INVALID;
+  if (h->nonsym) return HM_ERR_STATE;        // the file of a non-symmetric system is the input
   FILE* f = fopen(path, "wb");
   if (!f) return HM_ERR_IO;
   auto put = [&](const void* p, size_t sz) { return fwrite(p, 1, sz, f) == sz; };
@@ -1719,6 +1761,7 @@ hm_status hm_destroy(hm_handle h) {
   cudaFree(h->d_near);
   cudaFree(h->d_far);
   cudaFree(h->d_alpha);
+  cudaFree(h->d_alphaL);
   cudaFree(h->d_dinv);
   cudaFree(h->d_tinv);
   for (int i = 0; i < NPHYS; ++i) cudaFree(h->d_vec[i]);

@@ -57,7 +57,7 @@ enum { P_B = 0, P_BO = 1, P_Y = 2, P_Z = 3, P_IT = 4, P_XT = 5, P_R = 6,
        P_X0 = 11, P_B0 = 12,  // FP64 refinement: saved x and b
        NPHYS = 13 };
 // matrix buffers
-enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3, AB_TINV = 4 };
+enum { AB_NEAR = 0, AB_FAR = 1, AB_ALPHA = 2, AB_DINV = 3, AB_TINV = 4, AB_ALPHAL = 5 };
 
 // A launch-ready list of tasks (device copies of the host vectors).
 struct TaskList {
@@ -78,7 +78,16 @@ struct TaskList {
   int n_units = 0;
   // one-RHS bulk-copy kernel usable for this list (-1: not checked yet)
   mutable int bulk_ok = -1;
+  // matrix buffers (bit AB_*) its items read, set at upload: a launch whose
+  // table leaves one of them null returns an error instead of running
+  unsigned abuf_mask = 0;
 };
+// every matrix buffer a list reads is bound (abuf_mask against the table)
+inline bool abufs_bound(const TaskList& tl, const ABufs& ab) {
+  for (int b = 0; b < MAX_ABUF; ++b)
+    if (((tl.abuf_mask >> b) & 1u) && !ab.p[b]) return false;
+  return true;
+}
 // per-task row scale exponents of a task list (FP64-accurate tensor products)
 struct RowExp {
   std::vector<int> e;
@@ -148,6 +157,12 @@ struct hm_ctx {
   hm::cplx* d_tinv = nullptr;              // T_G = (I - A_G^T)^-1, row-major
   double wavelength = 1.0, k = 0.0;
   bool has_scaling = false;
+  // non-symmetric system (imported CFIE): every near and far block is stored
+  // for its own order and applied one way, and the forward sweep applies the
+  // left coefficients (stored transposed, in alpha's layout and offsets)
+  bool nonsym = false;
+  std::vector<hm::cplx> h_alphaL;
+  hm::cplx* d_alphaL = nullptr;
   // device data
   int* d_perm = nullptr;
   hm::cplx* d_near = nullptr;   long long near_elems = 0;

@@ -770,6 +770,7 @@ static void launch_tl(const TaskList& tl, const VBufs& vb, const ABufs& ab, int 
 hm_status launch_tasks(const TaskList& tl, const VBufs& vb, const ABufs& ab, int nrhs,
                        cudaStream_t s, int prec, long long spin_limit, int* err) {
   if (tl.tasks.empty()) return HM_OK;
+  if (!abufs_bound(tl, ab)) return HM_ERR_STATE;
   static bool attr = false;
   if (!attr) {
     HM_CUDA(cudaFuncSetAttribute(k_gemv_bulk<double2>,

@@ -807,6 +807,7 @@ hm_status launch_tasks_oz(const TaskList& tl, const VBufs& vb, const ABufs& ab, 
                           long long spin_limit, int* err, bool panels32) {
   if (tl.tasks.empty() || tl.n_units == 0) return HM_OK;
   if (xp.G * 8 < nrhs || xp.G % 16 != 0 || !tl.d_units) return HM_ERR_INVALID;
+  if (!abufs_bound(tl, ab)) return HM_ERR_STATE;
   static bool attr = false;
   static int nsm = 0;
   if (!attr) {

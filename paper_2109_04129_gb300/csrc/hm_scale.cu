@@ -314,7 +314,7 @@ extern "C" {
 
 hm_status hm_compute_scaling(hm_handle h) {
   if (!h) return HM_ERR_INVALID;
-  if (h->near.empty()) return HM_ERR_STATE;
+  if (h->near.empty() || h->nonsym) return HM_ERR_STATE;   // symmetric elimination only
   cplx *dZ = nullptr, *dZd = nullptr, *dW = nullptr, *dA = nullptr, *dD = nullptr;
   BTask* dT = nullptr;
   CopyJob* dC = nullptr;

@@ -247,3 +247,28 @@ def test_dense_fill_and_hmatrix_from_dense():
     # the far blocks keep the SVD tolerance against the full matrix
     Zp = Z1[np.ix_(H.perm, H.perm)]
     assert np.linalg.norm(H.to_dense() - Zp) <= 1e-4 * np.linalg.norm(Zp)
+
+
+def test_nonsym_block_file_round_trip():
+    """The block file of a non-symmetric system (NONSYM01 section) gives back
+    every ordered near and far block and both sets of coefficients."""
+    import os
+    import tempfile
+    from oracle.export import read_blocks, write_blocks_nonsym
+    v, f, H, S, b = _cfie_small()
+    fd, path = tempfile.mkstemp(suffix=".hmps")
+    os.close(fd)
+    try:
+        write_blocks_nonsym(path, H, S)
+        d = read_blocks(path)
+        assert d.get("nonsym") and sorted(d["near"]) == sorted(H.near)
+        assert all(np.array_equal(d["near"][k], H.near[k]) for k in H.near)
+        key = lambda x: (x[1], x[3])
+        fa, fb = sorted(d["far"], key=key), sorted(H.far, key=key)
+        assert [x[:5] for x in fa] == [x[:5] for x in fb]
+        assert all(np.array_equal(x[5], y[5]) for x, y in zip(fa, fb))
+        assert d["rows"] == S.rows and d["elim"] == S.order
+        assert all(np.array_equal(d["alpha"][kj], S.alpha[kj]) for kj in S.alpha)
+        assert all(np.array_equal(d["alphaL"][kj], S.alphaL[kj]) for kj in S.alphaL)
+    finally:
+        os.unlink(path)
