@@ -132,7 +132,15 @@ hm_status hm_build(const double* verts_host, int nv, const int* tris_host, int n
 /* Load an H-matrix (and, if present, its scaling coefficients) from the
  * neutral block file: leaf order, near blocks, low-rank far blocks, alpha,
  * D^-1 (format in the package documentation).  p supplies the solve
- * options; its tree options are ignored. */
+ * options; its tree options are ignored.
+ * A file with the non-symmetric section (the CFIE of Eq. 8, whose matrix is
+ * not symmetric) gives a handle whose near and far blocks are stored for both
+ * orders and applied one way, and whose forward sweep (HM_OP_RT) applies the
+ * left scaling coefficients alphaL_kj = -Z~_jk D_k^-1 where the symmetric
+ * system applies alpha^T (Sec. III-A without Z = Z^T): x = R sum (-1)^n it_n,
+ * it_0 = D^-1 L b, it_n = D^-1 L Z_F R it_(n-1).  Such a handle runs the FP64
+ * chain only: HM_MIXED in p, or a supernode section in the file, give
+ * HM_ERR_INVALID; hm_compute_scaling and hm_save give HM_ERR_STATE. */
 hm_status hm_import(const char* path, const hm_params* p, hm_handle* out);
 
 /* Write the handle's H-matrix and scaling in the same file format
