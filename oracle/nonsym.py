@@ -205,11 +205,13 @@ def dense_cfie(verts, tris, wavelength=1.0, alpha=0.5, processes=1, chunk=64):
     return rwg, Z
 
 
-def hmatrix_from_dense(Zd, rwg, leaf_max, aca_tol=1e-4, eta=0.0):
+def hmatrix_from_dense(Zd, rwg, leaf_max, aca_tol=1e-4, eta=0.0, tree=None):
     """HMatrixGen of a dense matrix (original order) on the octree of the
-    mesh: near blocks sliced, far blocks cut to their truncated SVD.  Studies
-    (one fill serves every leaf cap)."""
-    tree = Octree(rwg.centre, leaf_max) if not eta else Octree(rwg.centre, leaf_max, eta)
+    mesh (or a given tree with the same interface, e.g. the binary tree of
+    oracle.study_leaf_size): near blocks sliced, far blocks cut to their
+    truncated SVD.  Studies (one fill serves every leaf cap)."""
+    if tree is None:
+        tree = Octree(rwg.centre, leaf_max) if not eta else Octree(rwg.centre, leaf_max, eta)
     near_pairs, far_pairs = tree.blocks()
     P, off = tree.perm, tree.leaf_off
     near = {(i, j): Zd[np.ix_(P[off[i]:off[i + 1]], P[off[j]:off[j + 1]])]

@@ -231,14 +231,19 @@ def cfie_study(a, v, f, procs):
     b = CFIE(rwg, 1.0, a.cfie).plane_wave([0.0], [0.0], [0])
     x_ref = np.linalg.solve(Zd, b)
     adm = f"eta {a.eta:g}" if a.eta is not None else "non-touching"
-    print(f"# icosphere L{a.level}, radius {a.radius} lambda, CFIE alpha {a.cfie}, octree, "
+    tree_name = "binary tree, leaf size" if a.binary is not None else "octree, leaf cap"
+    print(f"# icosphere L{a.level}, radius {a.radius} lambda, CFIE alpha {a.cfie}, {tree_name}, "
           f"admissibility {adm}, reference LU of the full matrix "
           f"(fill + LU {time.perf_counter() - t0:.0f} s)", flush=True)
     print("# cap leaves edge_min edge_med edge_max ratio_eq45 "
           + " ".join(f"err_{t}" for t in a.terms) + " seconds", flush=True)
     for cap in a.caps:
         t0 = time.perf_counter()
-        H = hmatrix_from_dense(Zd, rwg, int(cap), 1e-4, a.eta or 0.0)
+        if a.binary is not None:
+            tree = BinaryTree(rwg.centre, cap, a.eta)
+            H = hmatrix_from_dense(Zd, rwg, 0, 1e-4, tree=tree)
+        else:
+            H = hmatrix_from_dense(Zd, rwg, int(cap), 1e-4, a.eta or 0.0)
         S = compute_scaling_general(H, "A")
         errs, ratio = [], None
         for nt in a.terms:
