@@ -162,6 +162,13 @@ def test_general_scaling_reduces_to_the_symmetric_one():
     x2, r2 = series_solve_general(G, SG, B, 3)
     assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
     assert np.allclose(r1, r2, rtol=1e-12)
+    # reading B (fill kept to the near pattern) reduces the same way
+    SB = compute_scaling(H, "B")
+    SGB = compute_scaling_general(G, "B")
+    assert SGB.rows == SB.rows
+    sb = max(np.abs(a).max() for a in SB.alpha.values())
+    assert max(np.abs(SGB.alphaL[kj] - SB.alpha[kj].T).max() for kj in SB.alpha) <= 1e-12 * sb
+    assert max(np.abs(a - b).max() for a, b in zip(SGB.D, SB.D)) <= 1e-12 * sd
 
 
 @functools.lru_cache(maxsize=None)
